@@ -1,0 +1,127 @@
+"""Preconditioned primal-dual iteration, Algorithm 2 with fixed l2 bounds.
+
+Reading (checked against the Condat-Vu condition of Sec. 3.4): the dual
+variables are the paper's scaled ones, so that with kappa_1 = 1,
+kappa_2 = 1 / ||Psi^dagger||^2 and kappa_3 = 1 / ||U^{1/2} Phi||^2 the updates are
+
+  step 4   u_l   = F Z x~_l                      (inside Phi below)
+  step 5   P     = (I - S*_w)(P + X~)
+  step 7   A_d   = (I - S^{l21}_{w mu ||Psi||^2})(A_d + Psi_d^dagger X~)
+  step 8   A~    = sum_d Psi_d A_d
+  step 10  vbar  = v + U Theta G u = v + U Phi_l x~_l
+  step 11  v     = U^{1/2} (I - P_B(y, eps)) (U^{-1/2} vbar)
+  step 12/20  G  = kappa_1 P + kappa_2 A~ + kappa_3 Phi^dagger v
+  step 21  X     = P_+(X - tau G)
+  step 22  X~    = 2 X - X_prev
+  step 23  beta  = ||X - X_prev|| / ||X||
+
+Initial state: everything zero (the paper's "Given" does not fix it). Steps
+13-19 (adaptive bounds) are not applied: the simulations keep epsilon fixed.
+Data blocks: B = 1 per channel (M_l^b = I).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import prox, wavelets
+
+
+@dataclass
+class PDParams:
+    mu: float
+    tau: float = 0.33
+    kappa1: float = 1.0
+    kappa2: float = 1.0            # 1 / ||Psi^dagger||^2 = 1 for the normalised frame
+    kappa3: float = 1.0
+    psi_norm2: float = 1.0         # ||Psi^dagger||_S^2
+    levels: int = 4
+    w_nuc: object = 1.0            # scalar or (L,) nuclear weights
+    w_l21: object = 1.0            # scalar or (9, ny, nx) l2,1 row weights
+    use_nuclear: bool = True
+    use_l21: bool = True
+
+
+@dataclass
+class PDState:
+    X: np.ndarray
+    Xt: np.ndarray
+    P: np.ndarray
+    A: np.ndarray
+    v: np.ndarray
+    t: int = 0
+    beta: float = float("nan")
+    rho: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+
+def init_state(L: int, ny: int, nx: int, M_total: int) -> PDState:
+    z = np.zeros((L, ny, nx))
+    return PDState(X=z.copy(), Xt=z.copy(), P=z.copy(),
+                   A=np.zeros((wavelets.N_BASES, L, ny, nx)),
+                   v=np.zeros(M_total, dtype=np.complex128))
+
+
+def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=None) -> PDState:
+    """One iteration of Algorithm 2 (returns a new state)."""
+    L = st.X.shape[0]
+    Xt = st.Xt
+    # step 5: low rankness dual
+    if prm.use_nuclear:
+        P, _ = prox.nuclear_dual(st.P + Xt, prm.w_nuc, 1.0 / prm.kappa1)
+    else:
+        P = np.zeros_like(st.P)
+    # steps 7-8: joint average sparsity dual and its synthesis
+    if prm.use_l21:
+        Q = st.A + wavelets.psi_adjoint_cube(Xt, prm.levels)
+        A = prox.l21_dual(Q, prm.w_l21, prm.mu * prm.psi_norm2)
+        At = wavelets.psi_cube(A, prm.levels)
+    else:
+        A = np.zeros_like(st.A)
+        At = np.zeros_like(st.X)
+    # steps 4, 10-12: data fidelity duals
+    PhiXt = op.forward(Xt)
+    v = np.empty_like(st.v)
+    rho = np.empty(L)
+    for l in range(L):
+        a, b = op.offsets[l], op.offsets[l + 1]
+        Ul = None if U is None else U[a:b]
+        vbar = st.v[a:b] + (PhiXt[a:b] if Ul is None else Ul * PhiXt[a:b])
+        z = vbar if Ul is None else vbar / np.sqrt(Ul)
+        rho[l] = np.sqrt(np.sum(np.abs(z - y[a:b]) ** 2))
+        v[a:b] = prox.l2ball_dual(vbar, y[a:b], eps[l], Ul)
+    # steps 20-23: primal update
+    Gd = op.adjoint(v)
+    G = prm.kappa1 * P + prm.kappa2 * At + prm.kappa3 * Gd
+    Xn = prox.proj_positive(st.X - prm.tau * G)
+    Xtn = 2.0 * Xn - st.X
+    nx_ = np.sqrt(np.sum(Xn * Xn))
+    beta = np.sqrt(np.sum((Xn - st.X) ** 2)) / nx_ if nx_ > 0 else float("inf")
+    return PDState(X=Xn, Xt=Xtn, P=P, A=A, v=v, t=st.t + 1, beta=beta, rho=rho)
+
+
+def pd_solve(op, y, eps, prm: PDParams, iters: int, U=None, state: PDState | None = None,
+             callback=None) -> PDState:
+    st = state if state is not None else init_state(op.L, op.ny, op.nx, int(op.offsets[-1]))
+    for _ in range(iters):
+        st = pd_step(st, op, y, eps, prm, U)
+        if callback is not None:
+            callback(st)
+    return st
+
+
+def metric_norm2(dX, dP, dA, dv, op, prm: PDParams) -> float:
+    """Squared norm of a state difference in the primal-dual metric
+        M = [[I / tau, -K^*], [-K, diag(1 / sigma_i)]],  K = [I; Psi^dagger; Phi],
+    written for the scaled duals (y_i = kappa_i D_i, sigma_i = kappa_i):
+        ||dX||^2 / tau - 2 sum_i kappa_i <K_i dX, dD_i> + sum_i kappa_i ||dD_i||^2.
+    The iteration is a proximal-point step in M (U = I), so the residual between
+    consecutive pairs (X^{t-1}, D^t) is nonincreasing."""
+    s = np.sum(dX * dX) / prm.tau
+    s += prm.kappa1 * (np.sum(dP * dP) - 2.0 * np.sum(dX * dP))
+    KdX = wavelets.psi_adjoint_cube(dX, prm.levels)
+    s += prm.kappa2 * (np.sum(dA * dA) - 2.0 * np.sum(KdX * dA))
+    PhidX = op.forward(dX)
+    s += prm.kappa3 * (np.sum(np.abs(dv) ** 2) - 2.0 * np.sum(np.real(np.conj(PhidX) * dv)))
+    return float(s)
