@@ -1,0 +1,288 @@
+/*
+ * hypersara.h - C ABI of the GB300 HyperSARA primal-dual hot path.
+ *
+ * Operations follow Abdulaziz, Dabbech & Wiaux, "Wideband super-resolution
+ * imaging in radio interferometry via low rankness and joint average sparsity
+ * models (HyperSARA)":
+ *   - measurement operator Phi_l = Theta_l G_l F Z and its adjoint
+ *     (Sec. 2.1, Eq. "inverse"; adjoint in Sec. 3.2 after Eq. "min-problem-d");
+ *   - SARA dictionary Psi^dagger / Psi: Dirac + Daubechies 1-8 (Sec. 2.3);
+ *   - proximity operators (Sec. 3.3, Eqs. "proj-plus", "prox-L*", "prox-L21")
+ *     and their Moreau duals (Eq. "md");
+ *   - one iteration of the preconditioned primal-dual algorithm (Algorithm 2,
+ *     steps 2-12 and 20-23, fixed l2 bounds, one data block per channel).
+ *
+ * Conventions shared by every entry point
+ *   Precision   a plan is FP32 (HS_F32: real = float, complex = float2 {re, im})
+ *               or FP64 (HS_F64: real = double, complex = double2). Every
+ *               real/complex buffer passed to that plan uses its precision.
+ *               l2-ball norms, epsilon, singular values, weights of the nuclear
+ *               norm and the Gram eigendecomposition are always FP64.
+ *   Layout      image cube X: L x ny x nx reals, channel-major, row-major images;
+ *               pixel (iy, ix) has centred coordinates (ix - nx/2, iy - ny/2).
+ *               coefficient cube A: 9 x L x ny x nx reals; basis 0 is Dirac,
+ *               basis p (1..8) the Mallat-layout periodic DWT with db_p; the
+ *               whole frame is scaled by 1/3 so that Psi Psi^dagger = I.
+ *               visibilities: sum_l M_l complex values, channel-concatenated in
+ *               the order the plan was created with (the "caller order").
+ *   Memory      pointers named "device" are CUDA device pointers the caller owns;
+ *               the library never frees them and keeps no reference after the
+ *               call returns, except where a create function says so. Plans and
+ *               states own only what they derive (sorted coordinates, tile lists,
+ *               tables, scratch), allocated at creation: the compute entry points
+ *               allocate nothing.
+ *   Streams     `stream` is a cudaStream_t (NULL = legacy default stream). Compute
+ *               entry points are asynchronous on it unless stated otherwise.
+ *               One plan or state must not be used from two streams at once
+ *               (they share scratch).
+ *   Errors      every function returns an hs_status; argument errors are detected
+ *               on the host before any launch and leave outputs untouched.
+ *               hs_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef HYPERSARA_H
+#define HYPERSARA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HS_API __attribute__((visibility("default")))
+#else
+#define HS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_ARG = -1,      /* invalid argument (null pointer, size, mode) */
+    HS_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    HS_ERR_NOMEM = -3,    /* device or host allocation failed at creation */
+    HS_ERR_TIMEOUT = -4,  /* a bounded device-side wait gave up */
+    HS_ERR_STATE = -5     /* object used in the wrong state */
+} hs_status;
+
+typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
+
+/* plan flags */
+#define HS_PLAN_COMPENSATED 1u   /* FP32 gridding with compensated (Kahan) summation */
+
+typedef struct hs_plan* hs_plan_t;
+typedef struct hs_pd_state* hs_pd_state_t;
+
+/* Library version and build information (static string). */
+HS_API const char* hs_version(void);
+
+/* Thread-local description of the last error ("" if none). */
+HS_API const char* hs_last_error(void);
+
+/*
+ * hs_plan_create - measurement setup for one wideband problem (Sec. 2.1).
+ *   nx, ny        image size; powers of two, >= 16, divisible by 2^wavelet_levels.
+ *   L             number of channels, 1..1024 (the nuclear-norm prox needs L <= 64).
+ *   vis_offsets   HOST array of L+1 int64: visibilities of channel l are
+ *                 [vis_offsets[l], vis_offsets[l+1]); vis_offsets[0] = 0,
+ *                 nondecreasing; empty channels are allowed; total < 2^31.
+ *   uv            DEVICE array (total x 2) of the plan's real type: (u, v) in
+ *                 radians, u pairs with the x axis; values must lie in [-pi, pi).
+ *                 Read once during the call (copied to the host and sorted).
+ *   weights       DEVICE array (total) of the plan's real type: diagonal natural
+ *                 weights Theta (Sec. 2.1), or NULL for Theta = I. Copied.
+ *   precond       DEVICE array (total) of the plan's real type: diagonal
+ *                 preconditioner U > 0 (Sec. 3.3), or NULL for U = I. Copied.
+ *                 Used by hs_op_norm2 and the primal-dual states.
+ *   oversample    grid oversampling o; must be 2.
+ *   J             interpolation kernel support; must be 8.
+ *   kb_beta       Kaiser-Bessel shape; <= 0 selects pi sqrt((J/o)^2 (o-1/2)^2 - 0.8).
+ *   wavelet_levels  DWT levels of the SARA bases, 1..8.
+ *   prec          HS_F32 or HS_F64.
+ *   flags         bitwise OR of HS_PLAN_* flags.
+ *   stream        stream used for the set-up copies; the call synchronises it.
+ * On success *out owns device memory until hs_plan_destroy. Errors: HS_ERR_ARG
+ * (sizes, uv outside [-pi, pi) or non-finite, bad offsets), HS_ERR_NOMEM, HS_ERR_CUDA.
+ */
+HS_API hs_status hs_plan_create(hs_plan_t* out, int nx, int ny, int L, const int64_t* vis_offsets,
+                         const void* uv, const void* weights, const void* precond,
+                         int oversample, int J, double kb_beta, int wavelet_levels,
+                         hs_prec prec, unsigned flags, void* stream);
+
+/* Frees everything the plan owns. The caller must make sure no work using the
+ * plan is still running. NULL is accepted. */
+HS_API hs_status hs_plan_destroy(hs_plan_t plan);
+
+/* Sizes derived by a plan (all host values). */
+typedef struct {
+    int nx, ny, L, Kx, Ky, levels, prec, flags;
+    int64_t total_vis;
+    int64_t grid_tile_entries;    /* visibility-tile pairs in the gridding lists */
+    int tile_x, tile_y;           /* gridding tile size in grid cells */
+    int kb_terms;                 /* coefficients per kernel polynomial piece */
+    double kb_beta;
+    double kb_fit_max_err;        /* max |poly - phi| / phi(0) of the kernel fit */
+    int64_t device_bytes;         /* device memory held by the plan */
+} hs_plan_info_t;
+
+HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);
+
+/*
+ * hs_phi_fwd - Y = Phi(X): Y_l = Theta_l G_l F Z x_l for every channel
+ * (Sec. 2.1, Eq. "inverse"). X: DEVICE L x ny x nx reals. Y: DEVICE total
+ * complex values, caller order. F is the unnormalised DFT with a negative
+ * exponent; G_l interpolates the spectrum with the separable Kaiser-Bessel
+ * kernel over 8 x 8 cells at t = u K / (2 pi).
+ */
+HS_API hs_status hs_phi_fwd(hs_plan_t plan, const void* X, void* Y, void* stream);
+
+/*
+ * hs_phi_adj - X = Phi^dagger(Y): x_l = Re(Z^T F^H G_l^H Theta_l y_l)
+ * (adjoint stated after Eq. "min-problem-d"; Re because x_l is real, Sec. 2.1).
+ * Y: DEVICE total complex (caller order). X: DEVICE L x ny x nx reals.
+ */
+HS_API hs_status hs_phi_adj(hs_plan_t plan, const void* Y, void* X, void* stream);
+
+/*
+ * hs_psi_fwd - A = Psi^dagger X (analysis, Sec. 2.3): for every channel,
+ * A[0] = x / 3 and A[p] = W_p x / 3 (p = 1..8), W_p the periodic orthonormal
+ * 2-D DWT with db_p, Mallat layout. X: DEVICE L x ny x nx; A: DEVICE 9 x L x ny x nx.
+ */
+HS_API hs_status hs_psi_fwd(hs_plan_t plan, const void* X, void* A, void* stream);
+
+/*
+ * hs_psi_adj - X = Psi A = (A[0] + sum_p W_p^T A[p]) / 3 (synthesis, the
+ * adjoint and, for this frame, the left inverse of hs_psi_fwd).
+ */
+HS_API hs_status hs_psi_adj(hs_plan_t plan, const void* A, void* X, void* stream);
+
+/*
+ * hs_prox_l21 - row-wise soft threshold over channels (Eq. "prox-L21").
+ * Row n = (basis b, pixel) collects A[b][0..L-1][pixel]. With
+ * lambda_n = thr * w_rows[n] (w_rows: DEVICE 9 x ny x nx reals, or NULL for 1):
+ *   dual = 0:  out_n = max(||a_n|| - lambda_n, 0) a_n / ||a_n||   (0 for a zero row)
+ *   dual = 1:  out_n = a_n - prox(a_n) = a_n min(1, lambda_n / ||a_n||)   (Eq. "md")
+ * A and out: DEVICE 9 x L x ny x nx; out may equal A. thr >= 0.
+ */
+HS_API hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, double thr,
+                      int dual, void* out, void* stream);
+
+/*
+ * hs_prox_nuclear - singular value soft threshold of the N x L matrix whose
+ * column l is channel l (Eq. "prox-L*"), through the L x L Gram matrix
+ * Z^T Z (FP64 accumulation) and its FP64 Jacobi eigendecomposition:
+ *   dual = 0:  out = U diag(max(s - thr w, 0)) V^T
+ *   dual = 1:  out = X - prox(X) = U diag(min(s, thr w)) V^T
+ * w_sv: DEVICE L doubles (weight of the j-th largest singular value) or NULL
+ * for 1. sv_out: DEVICE L doubles receiving the singular values of X in
+ * descending order, or NULL. Requires L <= 64. out may equal X.
+ */
+HS_API hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, double thr,
+                          int dual, void* out, double* sv_out, void* stream);
+
+/*
+ * hs_proj_l2ball - per-channel projection onto B(y_l, eps_l) =
+ * {z : ||z - y_l||_2 <= eps_l} (Sec. 3.2, functions g_l):
+ *   dual = 0:  out_l = P_B(z_l) = y_l + (z_l - y_l) min(1, eps_l / ||z_l - y_l||)
+ *   dual = 1:  out_l = z_l - P_B(z_l)
+ * Z, Yd, out: DEVICE total complex (caller order); eps: DEVICE L doubles >= 0.
+ * The norms are accumulated in FP64. rho_out: DEVICE L doubles receiving
+ * ||z_l - y_l||, or NULL. out may equal Z.
+ */
+HS_API hs_status hs_proj_l2ball(hs_plan_t plan, const void* Z, const void* Yd, const double* eps,
+                         int dual, void* out, double* rho_out, void* stream);
+
+/*
+ * hs_norm_l21 - sum_n w_n ||a_n||_2 over the rows of a coefficient cube
+ * (the weighted l2,1 norm of Sec. 2.3). w_rows as in hs_prox_l21. The result is
+ * written to *out_host after the stream has been synchronised.
+ */
+HS_API hs_status hs_norm_l21(hs_plan_t plan, const void* A, const void* w_rows, double* out_host,
+                      void* stream);
+
+/*
+ * hs_op_norm2 - max_l ||U_l^{1/2} Phi_l||_S^2 by power iteration on
+ * Phi_l^dagger U_l Phi_l, all channels at once (step sizes, Sec. 3.4).
+ * Start vector drawn from `seed`; stops when every channel's estimate changes
+ * by less than tol (relative) or after `iters` iterations. Synchronous:
+ * *out_host is valid on return. Uses plan scratch.
+ */
+HS_API hs_status hs_op_norm2(hs_plan_t plan, int iters, double tol, uint64_t seed, double* out_host,
+                      void* stream);
+
+/* Parameters of Algorithm 2 (Sec. 3.4); see hs_pd_state_create. */
+typedef struct {
+    double tau;         /* primal step, 0 < tau; convergence needs tau (k1 + k2 + k3 ||U^1/2 Phi||^2) < 1 */
+    double kappa1;      /* weight of the nuclear dual, default 1 */
+    double kappa2;      /* weight of the sparsity dual, 1 / ||Psi^dagger||^2 = 1 */
+    double kappa3;      /* weight of the data duals, 1 / ||U^1/2 Phi||^2 */
+    double mu;          /* regularisation parameter of the l2,1 term (Sec. 2.3) */
+    double psi_norm2;   /* ||Psi^dagger||_S^2 = 1 for the normalised frame */
+    int use_nuclear;    /* 0 drops the low-rankness prior (LR / JAS variants) */
+    int use_l21;        /* 0 drops the joint-sparsity prior */
+    const double* w_nuc;   /* DEVICE L doubles (nuclear weights) or NULL = 1; referenced, not copied */
+    const void* w_l21;     /* DEVICE 9 x ny x nx reals (row weights) or NULL = 1; referenced */
+} hs_pd_params;
+
+/*
+ * hs_pd_state_create - primal-dual state for Algorithm 2 with one block per
+ * channel and fixed l2 bounds. Y: DEVICE total complex data y_l (caller order,
+ * copied). eps: DEVICE L doubles (copied). All primal and dual variables start
+ * at zero. The state keeps references to params->w_nuc / w_l21, which must stay
+ * valid while it is used. Errors: HS_ERR_ARG, HS_ERR_NOMEM, HS_ERR_CUDA.
+ */
+HS_API hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
+                             const hs_pd_params* params, hs_pd_state_t* out, void* stream);
+
+HS_API hs_status hs_pd_state_destroy(hs_pd_state_t state);
+
+/*
+ * hs_pd_set_data - replace the data y_l (DEVICE total complex, caller order) and
+ * the bounds eps (DEVICE L doubles) of a state, keeping its primal and dual
+ * variables (warm start on new data of the same coverage). Asynchronous.
+ */
+HS_API hs_status hs_pd_set_data(hs_pd_state_t state, const void* Y, const double* eps, void* stream);
+
+/* One iteration of Algorithm 2 (steps 2-12 and 20-23), asynchronous on stream. */
+HS_API hs_status hs_pd_step(hs_pd_state_t state, void* stream);
+
+/*
+ * hs_pd_solve - `iters` iterations. graph = 1 captures one iteration as a CUDA
+ * graph on first use and replays it; graph = 0 launches kernels directly.
+ * Asynchronous on stream.
+ */
+HS_API hs_status hs_pd_solve(hs_pd_state_t state, int iters, int graph, void* stream);
+
+/*
+ * hs_pd_get - copy the current primal estimate X (DEVICE L x ny x nx, may be
+ * NULL) and the last iteration's diagnostics: *beta_host = ||X - X_prev|| / ||X||
+ * (Algorithm 2 step 23) and rho_host[l] = ||U^{-1/2} vbar_l - y_l|| (HOST L
+ * doubles, may be NULL). Synchronises the stream when beta_host or rho_host is
+ * given.
+ */
+HS_API hs_status hs_pd_get(hs_pd_state_t state, void* X, double* beta_host, double* rho_host,
+                    void* stream);
+
+/* Number of kernel nodes in the state's captured iteration graph (0 before the
+ * first hs_pd_solve with graph = 1): the kernel launches of one iteration. */
+HS_API hs_status hs_pd_graph_kernels(hs_pd_state_t state, int* out);
+
+/* Number of iterations performed by a state. */
+HS_API hs_status hs_pd_iterations(hs_pd_state_t state, int64_t* out);
+
+/*
+ * Host-only helpers (no GPU needed). Used by the plan; exported so that the
+ * derived tables can be inspected.
+ * hs_daubechies_lowpass: db_p low-pass filter, p = 1..8, by spectral
+ *   factorisation (Daubechies, Ten Lectures 6.1), minimum phase, sum = sqrt 2;
+ *   writes 2p doubles to out.
+ * hs_kb_poly_fit: piecewise polynomial fit of the Kaiser-Bessel kernel used by
+ *   the gridding kernels; returns the maximum error relative to phi(0) for
+ *   the given number of coefficients per unit interval.
+ */
+HS_API hs_status hs_daubechies_lowpass(int p, double* out);
+HS_API hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYPERSARA_H */

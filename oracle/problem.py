@@ -88,6 +88,8 @@ def op_norm2(op: nufft.WidebandOperator, U=None, iters: int = 500, tol: float = 
     rng = np.random.Generator(np.random.PCG64(seed))
     best = 0.0
     for l, ch in enumerate(op.ch):
+        if ch.M == 0:
+            continue
         Ul = None if U is None else U[op.offsets[l]:op.offsets[l + 1]]
         x = rng.standard_normal((op.ny, op.nx))
         x /= np.linalg.norm(x)

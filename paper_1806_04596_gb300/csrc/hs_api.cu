@@ -1,0 +1,571 @@
+// C ABI of the HyperSARA GB300 library: argument checks, plan / state
+// lifetime, operator entry points and the primal-dual iteration (Algorithm 2).
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+const char* last_error();
+hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, const void* uv,
+                      const void* weights, const void* precond, int oversample, int J, double kb_beta,
+                      int levels, hs_prec prec, unsigned flags, cudaStream_t s);
+void plan_free(Plan* p);
+}  // namespace hs
+
+using namespace hs;
+
+struct hs_plan {
+    Plan* p;
+};
+
+// Primal-dual state: variables of Algorithm 2 plus its own scratch, so that a
+// state never shares partial-sum buffers between its two concurrent branches.
+struct hs_pd_state {
+    Plan* p = nullptr;
+    hs_pd_params prm{};
+    void* X = nullptr;      // L x N reals: primal estimate
+    void* Xt = nullptr;     // L x N: extrapolated 2 X - X_prev
+    void* P = nullptr;      // L x N: nuclear dual
+    void* A = nullptr;      // 9 x L x N: sparsity duals
+    void* W = nullptr;      // 9 x L x N: Psi^dagger X~ scratch
+    void* At = nullptr;     // L x N: sum_d Psi_d A_d
+    void* D = nullptr;      // L x N: Phi^dagger v
+    void* v = nullptr;      // M complex (plan order): data duals
+    void* y = nullptr;      // M complex (plan order): data
+    void* d = nullptr;      // M complex: U^{-1/2} vbar - y
+    double* eps = nullptr;  // L
+    double* rho = nullptr;  // L
+    void* scale = nullptr;  // L reals
+    double* beta = nullptr; // 1
+    double* ppart = nullptr;   // primal partial sums
+    double* dpart = nullptr;   // de-gridding partial sums
+    int nprim = 0;
+    int nbx = 0;
+    int64_t iters = 0;
+    cudaStream_t side = nullptr, cap = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<void*> allocs;
+};
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define CHECK_PLAN(pl)                                                         \
+    do {                                                                       \
+        if ((pl) == nullptr || (pl)->p == nullptr)                             \
+            return fail(HS_ERR_ARG, "%s: plan is null", __func__);             \
+    } while (0)
+
+extern "C" {
+
+const char* hs_version(void) { return "hypersara-gb300 0.1 (sm_103a)"; }
+
+const char* hs_last_error(void) { return hs::last_error(); }
+
+hs_status hs_daubechies_lowpass(int p, double* out) {
+    clear_error();
+    return daubechies_lowpass(p, out);
+}
+
+hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err) {
+    clear_error();
+    if (J != 8 || terms < 2 || terms > 40 || max_rel_err == nullptr || !(beta > 0))
+        return fail(HS_ERR_ARG, "hs_kb_poly_fit: need J = 8, 2 <= terms <= 40, beta > 0");
+    std::vector<double> c;
+    *max_rel_err = kb_poly_fit(J, beta, terms, &c);
+    return HS_OK;
+}
+
+hs_status hs_plan_create(hs_plan_t* out, int nx, int ny, int L, const int64_t* vis_offsets,
+                         const void* uv, const void* weights, const void* precond, int oversample,
+                         int J, double kb_beta, int wavelet_levels, hs_prec prec, unsigned flags,
+                         void* stream) {
+    clear_error();
+    if (out == nullptr) return fail(HS_ERR_ARG, "hs_plan_create: out is null");
+    *out = nullptr;
+    Plan* p = nullptr;
+    HS_TRY(plan_create(&p, nx, ny, L, vis_offsets, uv, weights, precond, oversample, J, kb_beta,
+                       wavelet_levels, prec, flags, S(stream)));
+    hs_plan* h = new (std::nothrow) hs_plan;
+    if (h == nullptr) {
+        plan_free(p);
+        delete p;
+        return fail(HS_ERR_NOMEM, "hs_plan_create: host allocation failed");
+    }
+    h->p = p;
+    *out = h;
+    return HS_OK;
+}
+
+hs_status hs_plan_destroy(hs_plan_t plan) {
+    clear_error();
+    if (plan == nullptr) return HS_OK;
+    if (plan->p) {
+        plan_free(plan->p);
+        delete plan->p;
+    }
+    delete plan;
+    return HS_OK;
+}
+
+hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (info == nullptr) return fail(HS_ERR_ARG, "hs_plan_info: info is null");
+    const Plan* p = plan->p;
+    std::memset(info, 0, sizeof(*info));
+    info->nx = p->g.nx;
+    info->ny = p->g.ny;
+    info->L = p->g.L;
+    info->Kx = p->g.Kx;
+    info->Ky = p->g.Ky;
+    info->levels = p->levels;
+    info->prec = (int)p->prec;
+    info->flags = (int)p->flags;
+    info->total_vis = p->M_total;
+    info->grid_tile_entries = p->n_ent;
+    info->tile_x = p->g.tx;
+    info->tile_y = p->g.ty;
+    info->kb_terms = p->kb_terms;
+    info->kb_beta = p->beta;
+    info->kb_fit_max_err = p->kb_fit_err;
+    info->device_bytes = p->device_bytes;
+    return HS_OK;
+}
+
+hs_status hs_phi_fwd(hs_plan_t plan, const void* X, void* Y, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    Plan* p = plan->p;
+    if (X == nullptr || (Y == nullptr && p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_phi_fwd: null buffer");
+    if (p->M_total == 0) return HS_OK;
+    HS_TRY(fft_forward(p, X, S(stream)));
+    DegridArgs a{};
+    a.mode = DOUT_CALLER;
+    a.out = Y;
+    return degrid(p, a, S(stream));
+}
+
+hs_status hs_phi_adj(hs_plan_t plan, const void* Y, void* X, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    Plan* p = plan->p;
+    if (X == nullptr || (Y == nullptr && p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_phi_adj: null buffer");
+    GridArgs a{};
+    a.mode = GIN_CALLER;
+    a.in = Y;
+    HS_TRY(grid(p, a, S(stream)));
+    return fft_adjoint(p, X, S(stream));
+}
+
+hs_status hs_psi_fwd(hs_plan_t plan, const void* X, void* A, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (X == nullptr || A == nullptr) return fail(HS_ERR_ARG, "hs_psi_fwd: null buffer");
+    if (X == A) return fail(HS_ERR_ARG, "hs_psi_fwd: X and A must not alias");
+    return dwt_analysis(plan->p, X, A, S(stream));
+}
+
+hs_status hs_psi_adj(hs_plan_t plan, const void* A, void* X, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (X == nullptr || A == nullptr) return fail(HS_ERR_ARG, "hs_psi_adj: null buffer");
+    if (X == A) return fail(HS_ERR_ARG, "hs_psi_adj: X and A must not alias");
+    return dwt_synthesis(plan->p, A, X, S(stream));
+}
+
+hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, double thr, int dual,
+                      void* out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (A == nullptr || out == nullptr) return fail(HS_ERR_ARG, "hs_prox_l21: null buffer");
+    if (!(thr >= 0.0) || !std::isfinite(thr)) return fail(HS_ERR_ARG, "hs_prox_l21: thr must be >= 0");
+    if (dual != 0 && dual != 1) return fail(HS_ERR_ARG, "hs_prox_l21: dual must be 0 or 1");
+    return l21_apply(plan->p, A, nullptr, w_rows, thr, dual, out, S(stream));
+}
+
+hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, double thr, int dual,
+                          void* out, double* sv_out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (X == nullptr || out == nullptr) return fail(HS_ERR_ARG, "hs_prox_nuclear: null buffer");
+    if (!(thr >= 0.0) || !std::isfinite(thr))
+        return fail(HS_ERR_ARG, "hs_prox_nuclear: thr must be >= 0");
+    if (dual != 0 && dual != 1) return fail(HS_ERR_ARG, "hs_prox_nuclear: dual must be 0 or 1");
+    if (plan->p->g.L > MAX_L_NUC)
+        return fail(HS_ERR_ARG, "hs_prox_nuclear: L = %d exceeds %d", plan->p->g.L, MAX_L_NUC);
+    return nuclear_apply(plan->p, X, nullptr, w_sv, thr, dual, out, sv_out, S(stream));
+}
+
+hs_status hs_proj_l2ball(hs_plan_t plan, const void* Z, const void* Yd, const double* eps, int dual,
+                         void* out, double* rho_out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    Plan* p = plan->p;
+    if (eps == nullptr || ((Z == nullptr || Yd == nullptr || out == nullptr) && p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_proj_l2ball: null buffer");
+    if (dual != 0 && dual != 1) return fail(HS_ERR_ARG, "hs_proj_l2ball: dual must be 0 or 1");
+    return ball_project(p, Z, Yd, eps, dual, out, rho_out, S(stream));
+}
+
+hs_status hs_norm_l21(hs_plan_t plan, const void* A, const void* w_rows, double* out_host,
+                      void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (A == nullptr || out_host == nullptr) return fail(HS_ERR_ARG, "hs_norm_l21: null buffer");
+    Plan* p = plan->p;
+    HS_TRY(l21_norm(p, A, w_rows, p->dscal, S(stream)));
+    HS_CHECK_CUDA(cudaMemcpyAsync(out_host, p->dscal, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+    HS_CHECK_CUDA(cudaStreamSynchronize(S(stream)));
+    return HS_OK;
+}
+
+// splitmix64 followed by Box-Muller: a fixed, documented start vector.
+static uint64_t splitmix64(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+hs_status hs_op_norm2(hs_plan_t plan, int iters, double tol, uint64_t seed, double* out_host,
+                      void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (out_host == nullptr || iters < 1 || !(tol >= 0.0))
+        return fail(HS_ERR_ARG, "hs_op_norm2: need out_host, iters >= 1, tol >= 0");
+    Plan* p = plan->p;
+    cudaStream_t s = S(stream);
+    const int L = p->g.L;
+    const int64_t n = (int64_t)L * p->N();
+    std::vector<double> h((size_t)n);
+    uint64_t st = seed;
+    for (int64_t i = 0; i < n; i += 2) {
+        const double u1 = ((splitmix64(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((splitmix64(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double r = std::sqrt(-2.0 * std::log(u1));
+        h[i] = r * std::cos(2.0 * M_PI * u2);
+        if (i + 1 < n) h[i + 1] = r * std::sin(2.0 * M_PI * u2);
+    }
+    if (p->prec == HS_F32) {
+        std::vector<float> f(h.begin(), h.end());
+        HS_CHECK_CUDA(cudaMemcpyAsync(p->xbuf, f.data(), n * sizeof(float), cudaMemcpyHostToDevice, s));
+        HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    } else {
+        HS_CHECK_CUDA(cudaMemcpyAsync(p->xbuf, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    double* nrm = p->dscal;
+    HS_TRY(channel_norms(p, p->xbuf, nrm, s));
+    HS_TRY(scale_channels(p, p->xbuf, nrm, s));
+    std::vector<double> lam(L, 0.0), prev(L, 0.0);
+    for (int it = 0; it < iters; ++it) {
+        if (p->M_total > 0) {
+            HS_TRY(fft_forward(p, p->xbuf, s));
+            DegridArgs da{};
+            da.mode = DOUT_SORTED_U;
+            da.out = p->vis;
+            HS_TRY(degrid(p, da, s));
+            GridArgs ga{};
+            ga.mode = GIN_SORTED;
+            ga.in = p->vis;
+            HS_TRY(grid(p, ga, s));
+            HS_TRY(fft_adjoint(p, p->xbuf, s));
+        } else {
+            HS_CHECK_CUDA(cudaMemsetAsync(p->xbuf, 0, n * p->rsize(), s));
+        }
+        HS_TRY(channel_norms(p, p->xbuf, nrm, s));
+        HS_CHECK_CUDA(cudaMemcpyAsync(lam.data(), nrm, sizeof(double) * L, cudaMemcpyDeviceToHost, s));
+        HS_CHECK_CUDA(cudaStreamSynchronize(s));
+        HS_TRY(scale_channels(p, p->xbuf, nrm, s));
+        bool conv = it > 0;
+        for (int l = 0; l < L; ++l)
+            if (std::fabs(lam[l] - prev[l]) > tol * lam[l]) conv = false;
+        prev = lam;
+        if (conv) break;
+    }
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    double best = 0.0;
+    for (int l = 0; l < L; ++l) best = std::max(best, lam[l]);
+    *out_host = best;
+    return HS_OK;
+}
+
+// ------------------------------------------------------------------ primal-dual state
+static hs_status st_alloc(hs_pd_state* st, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(HS_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    st->allocs.push_back(*ptr);
+    return HS_OK;
+}
+
+static void st_free(hs_pd_state* st) {
+    if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    if (st->graph) cudaGraphDestroy(st->graph);
+    if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->side) cudaStreamDestroy(st->side);
+    if (st->cap) cudaStreamDestroy(st->cap);
+    for (void* q : st->allocs) cudaFree(q);
+    st->allocs.clear();
+}
+
+__global__ void k_gather_c2(const float2* __restrict__ in, const int* __restrict__ perm,
+                            float2* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+__global__ void k_gather_z2(const double2* __restrict__ in, const int* __restrict__ perm,
+                            double2* __restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
+                             const hs_pd_params* prm, hs_pd_state_t* out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (out == nullptr || prm == nullptr || eps == nullptr || (Y == nullptr && plan->p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_pd_state_create: null argument");
+    *out = nullptr;
+    if (!(prm->tau > 0.0) || !std::isfinite(prm->kappa1) || !std::isfinite(prm->kappa2) ||
+        !std::isfinite(prm->kappa3) || !(prm->mu >= 0.0) || !(prm->psi_norm2 > 0.0))
+        return fail(HS_ERR_ARG, "hs_pd_state_create: invalid parameters");
+    Plan* p = plan->p;
+    if (prm->use_nuclear && p->g.L > MAX_L_NUC)
+        return fail(HS_ERR_ARG, "hs_pd_state_create: nuclear prior needs L <= %d", MAX_L_NUC);
+    cudaStream_t s = S(stream);
+    std::unique_ptr<hs_pd_state> st(new hs_pd_state());
+    st->p = p;
+    st->prm = *prm;
+    const int L = p->g.L;
+    const int64_t N = p->N();
+    const size_t rs = p->rsize(), cs = p->csize();
+    const int64_t M = p->M_total;
+    hs_status e = HS_OK;
+#define ALLOC(ptr, bytes)                                   \
+    do {                                                    \
+        e = st_alloc(st.get(), (void**)&(ptr), (bytes));    \
+        if (e != HS_OK) {                                   \
+            st_free(st.get());                              \
+            return e;                                       \
+        }                                                   \
+    } while (0)
+    ALLOC(st->X, L * N * rs);
+    ALLOC(st->Xt, L * N * rs);
+    ALLOC(st->P, L * N * rs);
+    ALLOC(st->A, NB * L * N * rs);
+    ALLOC(st->W, NB * L * N * rs);
+    ALLOC(st->At, L * N * rs);
+    ALLOC(st->D, L * N * rs);
+    ALLOC(st->v, M * cs);
+    ALLOC(st->y, M * cs);
+    ALLOC(st->d, M * cs);
+    ALLOC(st->eps, L * sizeof(double));
+    ALLOC(st->rho, L * sizeof(double));
+    ALLOC(st->scale, L * rs);
+    ALLOC(st->beta, sizeof(double));
+    st->nprim = 1024;
+    ALLOC(st->ppart, 2 * st->nprim * sizeof(double));
+    st->nbx = std::max(1, degrid_blocks_x(p));
+    ALLOC(st->dpart, (size_t)L * st->nbx * sizeof(double));
+#undef ALLOC
+    auto cu = [&](cudaError_t ce, const char* what) -> hs_status {
+        if (ce == cudaSuccess) return HS_OK;
+        st_free(st.get());
+        return fail(HS_ERR_CUDA, "hs_pd_state_create: %s: %s", what, cudaGetErrorString(ce));
+    };
+    HS_TRY(cu(cudaMemsetAsync(st->X, 0, L * N * rs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->Xt, 0, L * N * rs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->P, 0, L * N * rs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->A, 0, NB * L * N * rs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->At, 0, L * N * rs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->v, 0, std::max<int64_t>(M, 1) * cs, s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->beta, 0, sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->rho, 0, L * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemcpyAsync(st->eps, eps, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "eps"));
+    if (M > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>((M + 255) / 256, 8192);
+        if (p->prec == HS_F32) k_gather_c2<<<g, 256, 0, s>>>((const float2*)Y, p->perm, (float2*)st->y, M);
+        else k_gather_z2<<<g, 256, 0, s>>>((const double2*)Y, p->perm, (double2*)st->y, M);
+        HS_TRY(cu(cudaGetLastError(), "gather"));
+    }
+    HS_TRY(cu(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking), "stream"));
+    HS_TRY(cu(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking), "stream"));
+    HS_TRY(cu(cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming), "event"));
+    HS_TRY(cu(cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming), "event"));
+    HS_TRY(cu(cudaStreamSynchronize(s), "sync"));
+    *out = st.release();
+    return HS_OK;
+}
+
+hs_status hs_pd_set_data(hs_pd_state_t st, const void* Y, const double* eps, void* stream) {
+    clear_error();
+    if (st == nullptr || eps == nullptr || (Y == nullptr && st->p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_pd_set_data: null argument");
+    Plan* p = st->p;
+    cudaStream_t s = S(stream);
+    const int64_t M = p->M_total;
+    HS_CHECK_CUDA(cudaMemcpyAsync(st->eps, eps, p->g.L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (M > 0) {
+        const unsigned g = (unsigned)std::min<int64_t>((M + 255) / 256, 8192);
+        if (p->prec == HS_F32) k_gather_c2<<<g, 256, 0, s>>>((const float2*)Y, p->perm, (float2*)st->y, M);
+        else k_gather_z2<<<g, 256, 0, s>>>((const double2*)Y, p->perm, (double2*)st->y, M);
+        HS_CHECK_LAUNCH();
+    }
+    return HS_OK;
+}
+
+hs_status hs_pd_state_destroy(hs_pd_state_t st) {
+    clear_error();
+    if (st == nullptr) return HS_OK;
+    st_free(st);
+    delete st;
+    return HS_OK;
+}
+
+// One iteration of Algorithm 2 on stream s. The prior branch (steps 5, 7, 8)
+// runs on the state's side stream, forked and joined with events, so it
+// overlaps the data-fidelity branch (steps 4, 10-12 and Phi^dagger of step 20).
+static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
+    Plan* p = st->p;
+    const hs_pd_params& q = st->prm;
+    const int64_t n = (int64_t)p->g.L * p->N();
+    HS_CHECK_CUDA(cudaEventRecord(st->ev_fork, s));
+    HS_CHECK_CUDA(cudaStreamWaitEvent(st->side, st->ev_fork, 0));
+    // ---- priors (side stream)
+    if (q.use_nuclear)   // step 5: P = (I - S*_w)(P + X~), threshold w / kappa1
+        HS_TRY(nuclear_apply(p, st->P, st->Xt, q.w_nuc, 1.0 / q.kappa1, 1, st->P, nullptr, st->side));
+    if (q.use_l21) {     // steps 7-8
+        HS_TRY(dwt_analysis(p, st->Xt, st->W, st->side));
+        // A_d = (I - S^{l21}_{w mu ||Psi||^2})(A_d + Psi_d^dagger X~)
+        HS_TRY(l21_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side));
+        HS_TRY(dwt_synthesis(p, st->A, st->At, st->side));
+    }
+    HS_CHECK_CUDA(cudaEventRecord(st->ev_join, st->side));
+    // ---- data fidelity (main stream)
+    if (p->M_total > 0) {
+        HS_TRY(fft_forward(p, st->Xt, s));                        // step 4
+        DegridArgs da{};
+        da.mode = DOUT_PD;
+        da.v = st->v;
+        da.y = st->y;
+        da.d = st->d;
+        da.part = st->dpart;
+        HS_TRY(degrid(p, da, s));                                  // step 10 (+ residual norms)
+        HS_TRY(ball_scale_from_partials(p, st->dpart, st->nbx, st->eps, st->rho, st->scale, s));
+        GridArgs ga{};
+        ga.mode = GIN_PD;
+        ga.d = st->d;
+        ga.scale = st->scale;
+        ga.v = st->v;
+        HS_TRY(grid(p, ga, s));                                    // steps 11-12
+        HS_TRY(fft_adjoint(p, st->D, s));                          // Z^T F^H of step 20
+    } else {
+        HS_CHECK_CUDA(cudaMemsetAsync(st->D, 0, n * p->rsize(), s));
+    }
+    HS_CHECK_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
+    // ---- steps 20-23
+    HS_TRY(primal_update(p, n, st->P, st->At, st->D, q.kappa1, q.kappa2, q.kappa3, q.tau,
+                         q.use_nuclear, q.use_l21, st->X, st->Xt, st->ppart, st->nprim, s));
+    HS_TRY(beta_from_partials(st->ppart, st->nprim, st->beta, s));
+    return HS_OK;
+}
+
+hs_status hs_pd_step(hs_pd_state_t st, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_step: state is null");
+    HS_TRY(pd_step_launch(st, S(stream)));
+    st->iters += 1;
+    return HS_OK;
+}
+
+hs_status hs_pd_solve(hs_pd_state_t st, int iters, int graph, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_solve: state is null");
+    if (iters < 0 || (graph != 0 && graph != 1)) return fail(HS_ERR_ARG, "hs_pd_solve: bad arguments");
+    cudaStream_t s = S(stream);
+    if (!graph) {
+        for (int i = 0; i < iters; ++i) {
+            HS_TRY(pd_step_launch(st, s));
+            st->iters += 1;
+        }
+        return HS_OK;
+    }
+    if (st->gexec == nullptr) {
+        // capture one iteration on the state's own stream (the caller's stream may be the
+        // legacy default stream, which cannot be captured)
+        HS_CHECK_CUDA(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal));
+        hs_status e = pd_step_launch(st, st->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st->cap, &g);
+        if (e != HS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
+        if (ce != cudaSuccess) return fail(HS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        st->graph = g;
+        HS_CHECK_CUDA(cudaGraphInstantiate(&st->gexec, g, 0));
+    }
+    for (int i = 0; i < iters; ++i) {
+        HS_CHECK_CUDA(cudaGraphLaunch(st->gexec, s));
+        st->iters += 1;
+    }
+    return HS_OK;
+}
+
+hs_status hs_pd_get(hs_pd_state_t st, void* X, double* beta_host, double* rho_host, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_get: state is null");
+    cudaStream_t s = S(stream);
+    Plan* p = st->p;
+    if (X) HS_CHECK_CUDA(cudaMemcpyAsync(X, st->X, (size_t)p->g.L * p->N() * p->rsize(),
+                                         cudaMemcpyDeviceToDevice, s));
+    if (beta_host) HS_CHECK_CUDA(cudaMemcpyAsync(beta_host, st->beta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (rho_host) HS_CHECK_CUDA(cudaMemcpyAsync(rho_host, st->rho, sizeof(double) * p->g.L,
+                                                cudaMemcpyDeviceToHost, s));
+    if (beta_host || rho_host) HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    return HS_OK;
+}
+
+hs_status hs_pd_graph_kernels(hs_pd_state_t st, int* out) {
+    clear_error();
+    if (st == nullptr || out == nullptr) return fail(HS_ERR_ARG, "hs_pd_graph_kernels: null argument");
+    *out = 0;
+    if (st->graph == nullptr) return HS_OK;
+    size_t n = 0;
+    HS_CHECK_CUDA(cudaGraphGetNodes(st->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    HS_CHECK_CUDA(cudaGraphGetNodes(st->graph, nodes.data(), &n));
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        HS_CHECK_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *out = k;
+    return HS_OK;
+}
+
+hs_status hs_pd_iterations(hs_pd_state_t st, int64_t* out) {
+    clear_error();
+    if (st == nullptr || out == nullptr) return fail(HS_ERR_ARG, "hs_pd_iterations: null argument");
+    *out = st->iters;
+    return HS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,275 @@
+// Batched 2-D FFT of the oversampled grid with the zero-padding / scaling Z
+// fused into the first pass and the crop / scale / real part of Z^T fused
+// into the last pass (Sec. 2.1: Phi_l = Theta_l G_l F Z).
+//
+// F is applied as two batches of 1-D transforms (rows, then columns). Each
+// CTA transforms G lines held in shared memory with a self-sorting Stockham
+// schedule of radix-8 passes (one 8-point DFT per thread per pass, operands in
+// registers) and one final radix-4 or radix-2 pass when log2 K is not a
+// multiple of 3. The first pass loads straight from global memory through the
+// mode's gather (padding, scaling), the last pass stores straight to global
+// memory through the mode's scatter (layout, crop), so each line costs one
+// global read and one global write.
+//
+// Forward Phi:  X (L x ny x nx real) --rows--> tmp (L x ny x Kx) --cols--> grid (L x Ky x Kx)
+// Adjoint:      grid --cols, inverse, keep ny rows--> tmp --rows, inverse, crop--> X
+// Only the ny image rows are ever transformed along x: the other Ky - ny rows
+// of Z x are zero in the forward direction and discarded by Z^T in the adjoint.
+#include "hs_device.cuh"
+#include "hs_internal.h"
+
+namespace hs {
+
+enum FftMode { ROW_FWD = 0, COL_FWD = 1, COL_INV = 2, ROW_INV = 3 };
+
+template <typename R> struct FftArgs {
+    const void* in;
+    void* out;
+    const Cx<R>* tw;   // exp(-2 pi i m / K), m < K
+    const R* cxs;      // Z scale along x (nx)
+    const R* cys;      // Z scale along y (ny)
+    int K, G, n8, rlast, npass;
+    int nx, ny, Kx, Ky;
+};
+
+template <typename R, int MODE>
+__device__ __forceinline__ Cx<R> fft_load(const FftArgs<R>& a, int line, int k) {
+    typedef Cx<R> CT;
+    if (MODE == ROW_FWD) {
+        const int l = line / a.ny, iy = line - l * a.ny;
+        const int h = a.nx >> 1;
+        int ix;
+        if (k < h) ix = k + h;
+        else if (k >= a.Kx - h) ix = k - a.Kx + h;
+        else return cx<R>(0, 0);
+        const R* X = (const R*)a.in;
+        return cx<R>(a.cys[iy] * a.cxs[ix] * X[((int64_t)l * a.ny + iy) * a.nx + ix], (R)0);
+    } else if (MODE == COL_FWD) {
+        const int cpb = a.Kx;   // line = l * Kx + kx
+        const int l = line / cpb, kx = line - l * cpb;
+        const int h = a.ny >> 1;
+        int iy;
+        if (k < h) iy = k + h;
+        else if (k >= a.Ky - h) iy = k - a.Ky + h;
+        else return cx<R>(0, 0);
+        const CT* T = (const CT*)a.in;
+        return T[((int64_t)l * a.ny + iy) * a.Kx + kx];
+    } else if (MODE == COL_INV) {
+        const int l = line / a.Kx, kx = line - l * a.Kx;
+        const CT* Gd = (const CT*)a.in;
+        return Gd[((int64_t)l * a.Ky + k) * a.Kx + kx];
+    } else {   // ROW_INV
+        const int l = line / a.ny, iy = line - l * a.ny;
+        const CT* T = (const CT*)a.in;
+        return T[((int64_t)l * a.ny + iy) * a.Kx + k];
+    }
+}
+
+template <typename R, int MODE>
+__device__ __forceinline__ void fft_store(const FftArgs<R>& a, int line, int k, Cx<R> v) {
+    typedef Cx<R> CT;
+    if (MODE == ROW_FWD) {
+        CT* T = (CT*)a.out;
+        T[(int64_t)line * a.Kx + k] = v;   // line = l * ny + iy
+    } else if (MODE == COL_FWD) {
+        const int l = line / a.Kx, kx = line - l * a.Kx;
+        CT* Gd = (CT*)a.out;
+        Gd[((int64_t)l * a.Ky + k) * a.Kx + kx] = v;
+    } else if (MODE == COL_INV) {
+        const int l = line / a.Kx, kx = line - l * a.Kx;
+        const int h = a.ny >> 1;
+        int iy;
+        if (k < h) iy = k + h;
+        else if (k >= a.Ky - h) iy = k - a.Ky + h;
+        else return;
+        CT* T = (CT*)a.out;
+        T[((int64_t)l * a.ny + iy) * a.Kx + kx] = v;
+    } else {   // ROW_INV: crop, scale, real part
+        const int l = line / a.ny, iy = line - l * a.ny;
+        const int h = a.nx >> 1;
+        int ix;
+        if (k < h) ix = k + h;
+        else if (k >= a.Kx - h) ix = k - a.Kx + h;
+        else return;
+        R* X = (R*)a.out;
+        X[((int64_t)l * a.ny + iy) * a.nx + ix] = a.cys[iy] * a.cxs[ix] * v.x;
+    }
+}
+
+// One Stockham pass of radix RAD over the CTA's G lines: every thread owns
+// 8 / RAD butterflies (8 operands, all in registers).
+template <typename R, int DIR, int MODE, int RAD>
+__device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int Ns, bool first,
+                                         bool last, int line0) {
+    typedef Cx<R> CT;
+    constexpr bool COLS = (MODE == COL_FWD || MODE == COL_INV);
+    constexpr int PER = 8 / RAD;
+    const int K = a.K, G = a.G;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int nb = K / RAD;
+    CT v[8];
+    int gs[PER], js[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int w = tid + i * nthr;
+        const int g = COLS ? (w % G) : (w / nb);
+        const int j = COLS ? (w / G) : (w % nb);
+        gs[i] = g;
+        js[i] = j;
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+            const int k = j + r * nb;
+            v[i * RAD + r] = first ? fft_load<R, MODE>(a, line0 + g, k)
+                                   : sm[COLS ? (k * G + g) : (g * K + k)];
+        }
+    }
+    if (!first) __syncthreads();   // every read of this pass precedes any write
+    const int step = K / (Ns * RAD);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int j = js[i];
+        const int kk = j % Ns;
+        CT* u = v + i * RAD;
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+            CT t = a.tw[kk * r * step];
+            if (DIR > 0) t.y = -t.y;
+            u[r] = cmul(u[r], t);
+        }
+        if (RAD == 8) {
+            dft8<R, DIR>(u);
+        } else if (RAD == 4) {
+            dft4<DIR>(u[0], u[1], u[2], u[3]);
+        } else {
+            CT t0 = cadd(u[0], u[1]);
+            u[1] = csub(u[0], u[1]);
+            u[0] = t0;
+        }
+        const int base = (j / Ns) * Ns * RAD + kk;
+        const int g = gs[i];
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) {
+            const int k = base + r * Ns;
+            if (last) fft_store<R, MODE>(a, line0 + g, k, u[r]);
+            else sm[COLS ? (k * G + g) : (g * K + k)] = u[r];
+        }
+    }
+    __syncthreads();
+}
+
+// DIR = -1: forward transform (exp(-2 pi i kn / K)); DIR = +1: unnormalised inverse.
+template <typename R, int DIR, int MODE>
+__global__ void __launch_bounds__(1024) k_fft(FftArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<R>* sm = reinterpret_cast<Cx<R>*>(smem_raw);
+    const int line0 = blockIdx.x * a.G;
+    int Ns = 1;
+    for (int pass = 0; pass < a.npass; ++pass) {
+        const bool first = (pass == 0), last = (pass == a.npass - 1);
+        if (pass < a.n8) {
+            fft_pass<R, DIR, MODE, 8>(a, sm, Ns, first, last, line0);
+            Ns *= 8;
+        } else if (a.rlast == 4) {
+            fft_pass<R, DIR, MODE, 4>(a, sm, Ns, first, last, line0);
+            Ns *= 4;
+        } else {
+            fft_pass<R, DIR, MODE, 2>(a, sm, Ns, first, last, line0);
+            Ns *= 2;
+        }
+    }
+}
+
+static void radix_plan(int K, int* n8, int* rlast, int* npass) {
+    int p = 0;
+    while ((1 << p) < K) ++p;
+    *n8 = p / 3;
+    const int rem = p % 3;
+    *rlast = rem == 0 ? 8 : (1 << rem);
+    *npass = *n8 + (rem ? 1 : 0);
+}
+
+template <typename R, int DIR, int MODE>
+static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) {
+    FftArgs<R> a;
+    a.in = in;
+    a.out = out;
+    a.nx = p->g.nx;
+    a.ny = p->g.ny;
+    a.Kx = p->g.Kx;
+    a.Ky = p->g.Ky;
+    a.cxs = (const R*)p->cxs;
+    a.cys = (const R*)p->cys;
+    const bool cols = (MODE == COL_FWD || MODE == COL_INV);
+    const int K = cols ? p->g.Ky : p->g.Kx;
+    a.K = K;
+    a.tw = (const Cx<R>*)(cols ? p->twy : p->twx);
+    radix_plan(K, &a.n8, &a.rlast, &a.npass);
+    int G, nlines;
+    if (cols) {
+        G = 1024 / (K / 8);
+        if (G > 16) G = 16;
+        if (G > p->g.Kx) G = p->g.Kx;
+        nlines = p->g.L * p->g.Kx;
+    } else {
+        G = 256 / (K / 8);
+        if (G < 1) G = 1;
+        if (G > p->g.ny) G = p->g.ny;
+        nlines = p->g.L * p->g.ny;
+    }
+    if (G < 1) G = 1;
+    a.G = G;
+    const int threads = G * K / 8;
+    const size_t smem = (size_t)G * K * sizeof(Cx<R>);
+    const int blocks = nlines / G;
+    if (blocks == 0) return HS_OK;
+    k_fft<R, DIR, MODE><<<blocks, threads, smem, s>>>(a);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+template <typename R, int DIR, int MODE> static hs_status fft_attr() {
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft<R, DIR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
+    return HS_OK;
+}
+
+// Opt the FFT kernels into large dynamic shared memory (once per process, at
+// plan creation, outside any stream capture).
+hs_status fft_init() {
+    static bool done = false;
+    if (done) return HS_OK;
+    HS_TRY((fft_attr<float, -1, ROW_FWD>()));
+    HS_TRY((fft_attr<float, -1, COL_FWD>()));
+    HS_TRY((fft_attr<float, 1, COL_INV>()));
+    HS_TRY((fft_attr<float, 1, ROW_INV>()));
+    HS_TRY((fft_attr<double, -1, ROW_FWD>()));
+    HS_TRY((fft_attr<double, -1, COL_FWD>()));
+    HS_TRY((fft_attr<double, 1, COL_INV>()));
+    HS_TRY((fft_attr<double, 1, ROW_INV>()));
+    done = true;
+    return HS_OK;
+}
+
+hs_status fft_forward(Plan* p, const void* X, cudaStream_t s) {
+    if (p->prec == HS_F32) {
+        HS_TRY((launch_fft<float, -1, ROW_FWD>(p, X, p->tmp, s)));
+        HS_TRY((launch_fft<float, -1, COL_FWD>(p, p->tmp, p->grid, s)));
+    } else {
+        HS_TRY((launch_fft<double, -1, ROW_FWD>(p, X, p->tmp, s)));
+        HS_TRY((launch_fft<double, -1, COL_FWD>(p, p->tmp, p->grid, s)));
+    }
+    return HS_OK;
+}
+
+hs_status fft_adjoint(Plan* p, void* X, cudaStream_t s) {
+    if (p->prec == HS_F32) {
+        HS_TRY((launch_fft<float, 1, COL_INV>(p, p->grid, p->tmp, s)));
+        HS_TRY((launch_fft<float, 1, ROW_INV>(p, p->tmp, X, s)));
+    } else {
+        HS_TRY((launch_fft<double, 1, COL_INV>(p, p->grid, p->tmp, s)));
+        HS_TRY((launch_fft<double, 1, ROW_INV>(p, p->tmp, X, s)));
+    }
+    return HS_OK;
+}
+
+}  // namespace hs

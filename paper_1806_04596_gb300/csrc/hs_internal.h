@@ -1,0 +1,174 @@
+// Internal declarations of the HyperSARA GB300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hypersara.h"
+
+namespace hs {
+
+// ---------------------------------------------------------------- errors
+hs_status fail(hs_status st, const char* fmt, ...);
+void clear_error();
+
+#define HS_CHECK_CUDA(call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ::hs::fail(HS_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,    \
+                              cudaGetErrorString(e_));                                   \
+    } while (0)
+
+#define HS_CHECK_LAUNCH() HS_CHECK_CUDA(cudaGetLastError())
+
+#define HS_TRY(expr)                          \
+    do {                                      \
+        hs_status s_ = (expr);                \
+        if (s_ != HS_OK) return s_;           \
+    } while (0)
+
+// ---------------------------------------------------------------- constants
+constexpr int KB_J = 8;              // interpolation support (cells per axis)
+constexpr int NB = 9;                // SARA bases: Dirac + db1..db8
+constexpr int NW = 8;                // wavelet bases
+constexpr int MAXF = 16;             // longest filter (db8)
+constexpr int KB_TERMS_F32 = 9;      // polynomial coefficients per unit piece, FP32
+constexpr int KB_TERMS_F64 = 14;     // ... FP64
+constexpr int GRID_TILE = 32;        // gridding tile side (cells)
+constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumulators)
+constexpr int DEGRID_CHUNK = 256;    // visibilities per degridding CTA
+constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
+
+// Coordinates of one visibility in an FP64 plan: window start cells and the
+// fractional part of t = u K / (2 pi) (exact in FP64).
+struct Coord64 {
+    double fx, fy;
+    int cx, cy;   // floor(t) mod K per axis
+};
+
+// Sizes passed by value to kernels.
+struct Geo {
+    int nx, ny, L, Kx, Ky;
+    int fbx, fby;          // fractional bits of the FP32 fixed-point coordinates
+    int tx, ty, ntx, nty;  // gridding tile size and tiles per axis
+};
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+    Geo g{};
+    int levels = 4;
+    int J = 8, o = 2;
+    hs_prec prec = HS_F32;
+    unsigned flags = 0;
+    double beta = 0.0;
+    int kb_terms = 0;
+    double kb_fit_err = 0.0;
+    int64_t M_total = 0;
+    int Mmax = 0;
+    std::vector<int64_t> off_h;
+    int64_t* off_d = nullptr;          // L+1
+    int* perm = nullptr;               // sorted index -> caller index
+    void* coords = nullptr;            // FP32: uint2 fixed point; FP64: Coord64
+    void* w_sorted = nullptr;          // Theta in sorted order (real) or null
+    void* u_sorted = nullptr;          // U in sorted order (real) or null
+    int64_t n_ent = 0;
+    int64_t* tile_off = nullptr;       // L * ntiles + 1
+    int* tile_ent = nullptr;           // sorted visibility index per (channel, tile) entry
+    void* kbc = nullptr;               // 8 * kb_terms reals
+    void* cxs = nullptr;               // nx reals (Z scale along x)
+    void* cys = nullptr;               // ny reals
+    void* twx = nullptr;               // Kx complex, exp(-2 pi i m / Kx)
+    void* twy = nullptr;               // Ky complex
+    void* filt = nullptr;              // 8 * 2 * MAXF reals: lowpass, highpass per db_p
+    // scratch
+    void* grid = nullptr;              // L * Ky * Kx complex
+    void* tmp = nullptr;               // L * ny * Kx complex
+    void* vis = nullptr;               // M_total complex (sorted order)
+    void* dwt_a = nullptr;             // 8 * L * N reals
+    void* dwt_b = nullptr;             // 8 * L * N reals
+    double* part = nullptr;            // partial sums (size part_n doubles)
+    int64_t part_n = 0;
+    double* gram = nullptr;            // MAX_L_NUC^2 doubles
+    double* eigf = nullptr;            // MAX_L_NUC^2 doubles (factor matrix V diag(f) V^T)
+    double* sv = nullptr;              // MAX_L_NUC doubles
+    double* dscal = nullptr;           // small per-channel doubles (4 * L)
+    void* xbuf = nullptr;              // L * N reals (power iteration, misc)
+    void* xbuf2 = nullptr;             // L * N reals
+    int64_t device_bytes = 0;
+    std::vector<void*> allocs;
+
+    int64_t N() const { return (int64_t)g.nx * g.ny; }
+    int64_t ntiles() const { return (int64_t)g.ntx * g.nty; }
+    size_t rsize() const { return prec == HS_F64 ? 8 : 4; }
+    size_t csize() const { return 2 * rsize(); }
+};
+
+// Device allocation tracked by the plan (freed in destroy).
+hs_status plan_alloc(Plan* p, void** ptr, size_t bytes);
+
+// ---------------------------------------------------------------- host tables
+hs_status daubechies_lowpass(int p, double* out);
+double kb_phi(double x, int J, double beta);
+double kb_phihat(double f, int J, double beta);
+// Fits phi(m + f), f in [0,1), m = -J/2 .. J/2-1, as polynomials in s = 2f - 1
+// with `terms` coefficients each (ascending powers). Returns the max error / phi(0).
+double kb_poly_fit(int J, double beta, int terms, std::vector<double>* coef);
+
+// ---------------------------------------------------------------- launches
+// Visibility input / output modes of the gridding and de-gridding kernels.
+enum DegridOut { DOUT_CALLER = 0, DOUT_SORTED = 1, DOUT_SORTED_U = 2, DOUT_PD = 3 };
+enum GridIn { GIN_CALLER = 0, GIN_SORTED = 1, GIN_PD = 2 };
+
+// FFT stages (hs_fft.cu)
+hs_status fft_forward(Plan* p, const void* X, cudaStream_t s);           // X -> p->grid
+hs_status fft_adjoint(Plan* p, void* X, cudaStream_t s);                 // p->grid -> X
+
+// NUFFT interpolation (hs_nufft.cu)
+struct DegridArgs {
+    int mode;
+    void* out;              // DOUT_CALLER / DOUT_SORTED / DOUT_SORTED_U: destination
+    void* v;                // DOUT_PD: dual v (read), sorted
+    const void* y;          // DOUT_PD: data, sorted
+    void* d;                // DOUT_PD: output d = U^{-1/2} vbar - y, sorted
+    double* part;           // DOUT_PD: per-CTA partial ||d||^2, [L][blocks_x]
+};
+hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s);
+int degrid_blocks_x(const Plan* p);
+
+struct GridArgs {
+    int mode;
+    const void* in;         // GIN_CALLER / GIN_SORTED: visibilities
+    const void* d;          // GIN_PD: d from the de-gridding pass
+    const void* scale;      // GIN_PD: per-channel real factor max(0, 1 - eps / rho)
+    void* v;                // GIN_PD: dual output v (home tile writes), sorted
+};
+hs_status grid(Plan* p, const GridArgs& a, cudaStream_t s);
+
+// l2-ball helpers (hs_prox.cu)
+hs_status ball_scale_from_partials(Plan* p, const double* part, int nparts, const double* eps,
+                                   double* rho, void* scale_real, cudaStream_t s);
+
+// Wavelets (hs_dwt.cu)
+hs_status dwt_analysis(Plan* p, const void* X, void* A, cudaStream_t s);
+hs_status dwt_synthesis(Plan* p, const void* A, void* X, cudaStream_t s);
+
+// Proximal operators and PD pieces (hs_prox.cu)
+hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows, double thr,
+                    int dual, void* out, cudaStream_t s);
+hs_status l21_norm(Plan* p, const void* A, const void* w_rows, double* out_dev, cudaStream_t s);
+hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
+                        int dual, void* out, double* sv_out, cudaStream_t s);
+hs_status ball_project(Plan* p, const void* Z, const void* Yd, const double* eps, int dual,
+                       void* out, double* rho_out, cudaStream_t s);
+hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const void* D,
+                        double k1, double k2, double k3, double tau, int use_p, int use_a,
+                        void* X, void* Xt, double* part, int nparts, cudaStream_t s);
+hs_status beta_from_partials(const double* part, int nparts, double* beta, cudaStream_t s);
+hs_status channel_norms(Plan* p, const void* X, double* out_dev, cudaStream_t s);
+hs_status scale_channels(Plan* p, void* X, const double* norms, cudaStream_t s);
+
+}  // namespace hs

@@ -1,0 +1,379 @@
+// De-gridding G_l and gridding G_l^H with the 8 x 8 Kaiser-Bessel window
+// (Sec. 2.1: "G_l has a convolution kernel on its rows"), all channels in one
+// launch, fused with the data-fidelity dual update of Algorithm 2 steps 10-12.
+//
+// Kernel values are computed on the fly: phi(m + f) for the unit piece m is a
+// fitted polynomial in s = 2 f - 1 (FP32: 9 coefficients, error 7e-9 of phi(0);
+// FP64: 14 coefficients, 6e-15), so the 8 taps of one axis are 8 independent
+// Horner chains at the same s, one per lane.
+//
+// De-gridding: 8 lanes per visibility, lane j owns window column j and walks
+// the 8 rows (coalesced 64-byte row segments), then the 8 lanes reduce by
+// shuffles. Visibilities are processed in the plan's tile-sorted order so
+// neighbouring lanes touch neighbouring grid cells.
+//
+// Gridding: one CTA per (channel, 32 x 32 output tile) consumes the tile's list
+// of visibilities whose window overlaps it (built by the plan). Each warp adds
+// whole windows (two rows of 32 lanes) into its own private copy of the tile
+// in shared memory, so no atomics are needed anywhere; the copies are summed
+// in a fixed order and every output cell is written exactly once, so the
+// result is deterministic and the grid needs no zeroing pass. With
+// HS_PLAN_COMPENSATED the FP32 accumulation is Kahan-compensated.
+#include "hs_device.cuh"
+#include "hs_internal.h"
+
+namespace hs {
+
+template <typename R> struct VisCoord;
+template <> struct VisCoord<float> {
+    // fixed point: cell in the high bits, fraction in the low `fb` bits
+    static __device__ __forceinline__ void get(const void* c, int64_t i, const Geo& g, int& cxv,
+                                               int& cyv, float& fx, float& fy) {
+        const uint2 t = ((const uint2*)c)[i];
+        cxv = (int)(t.x >> g.fbx);
+        cyv = (int)(t.y >> g.fby);
+        fx = (float)(t.x & ((1u << g.fbx) - 1u)) * __int_as_float((127 - g.fbx) << 23);
+        fy = (float)(t.y & ((1u << g.fby) - 1u)) * __int_as_float((127 - g.fby) << 23);
+    }
+};
+template <> struct VisCoord<double> {
+    static __device__ __forceinline__ void get(const void* c, int64_t i, const Geo& g, int& cxv,
+                                               int& cyv, double& fx, double& fy) {
+        const Coord64 t = ((const Coord64*)c)[i];
+        cxv = t.cx;
+        cyv = t.cy;
+        fx = t.fx;
+        fy = t.fy;
+    }
+};
+
+template <typename R> struct NufftK {
+    Geo g;
+    const Cx<R>* grid;
+    Cx<R>* grid_out;
+    const void* coords;
+    const int64_t* off;
+    const R* w;        // Theta (sorted) or null
+    const R* u;        // U (sorted) or null
+    const int* perm;   // sorted -> caller
+    const R* kbc;      // 8 x NC coefficients
+    // de-gridding outputs / PD inputs
+    Cx<R>* out;
+    Cx<R>* v;
+    const Cx<R>* y;
+    Cx<R>* d;
+    double* part;
+    int nblk_x;
+    // gridding inputs
+    const Cx<R>* in;
+    const R* scale;
+    const int64_t* tile_off;
+    const int* tile_ent;
+};
+
+// ---------------------------------------------------------------- de-gridding
+template <typename R, int NC, int MODE>
+__global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
+    typedef Cx<R> CT;
+    __shared__ double red[32];
+    const int l = blockIdx.y;
+    const int64_t cbeg = a.off[l], cend = a.off[l + 1];
+    const int64_t beg = cbeg + (int64_t)blockIdx.x * DEGRID_CHUNK;
+    const int64_t end = min(cend, beg + DEGRID_CHUNK);
+    if (beg >= end) {
+        if (MODE == DOUT_PD && threadIdx.x == 0) a.part[(int64_t)l * a.nblk_x + blockIdx.x] = 0.0;
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 7;              // window column / tap owned by this lane
+    const int grp = threadIdx.x >> 3;    // 32 groups of 8 lanes
+    const int gbase = lane & ~7;
+    R c[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - j) * NC + k];
+    const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const CT* G = a.grid + (int64_t)l * Ky * Kx;
+    double sq = 0.0;
+    for (int64_t i0 = beg; i0 < end; i0 += 32) {
+        const int64_t iv = i0 + grp;
+        const bool valid = iv < end;
+        const int64_t i = valid ? iv : beg;
+        int cxv, cyv;
+        R fx, fy;
+        VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+        const int k0x = (cxv - 3) & (Kx - 1);
+        const int k0y = (cyv - 3) & (Ky - 1);
+        const R pu = horner<R, NC>(c, (R)2 * fx - (R)1);
+        const R pv = horner<R, NC>(c, (R)2 * fy - (R)1);
+        const int col = (k0x + j) & (Kx - 1);
+        CT acc = cx<R>(0, 0);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int row = (k0y + r) & (Ky - 1);
+            const CT gv = G[(int64_t)row * Kx + col];
+            const R pvr = __shfl_sync(0xffffffffu, pv, gbase + r);
+            acc.x = fma(pvr, gv.x, acc.x);
+            acc.y = fma(pvr, gv.y, acc.y);
+        }
+        acc.x *= pu;
+        acc.y *= pu;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (valid && j == 0) {
+            if (a.w) acc = cscale(acc, a.w[i]);
+            if (MODE == DOUT_CALLER) {
+                a.out[a.perm[i]] = acc;
+            } else if (MODE == DOUT_SORTED) {
+                a.out[i] = acc;
+            } else if (MODE == DOUT_SORTED_U) {
+                a.out[i] = a.u ? cscale(acc, a.u[i]) : acc;
+            } else {   // DOUT_PD: vbar = v + U Phi x~, d = U^{-1/2} vbar - y
+                CT vb = a.v[i];
+                CT dd;
+                if (a.u) {
+                    const R uu = a.u[i];
+                    const R is = (R)1 / sqrt(uu);
+                    vb.x = fma(uu, acc.x, vb.x);
+                    vb.y = fma(uu, acc.y, vb.y);
+                    dd = csub(cscale(vb, is), a.y[i]);
+                } else {
+                    dd = csub(cadd(vb, acc), a.y[i]);
+                }
+                a.d[i] = dd;
+                sq += (double)dd.x * (double)dd.x + (double)dd.y * (double)dd.y;
+            }
+        }
+    }
+    if (MODE == DOUT_PD) {
+        const double tot = block_sum(sq, red);
+        if (threadIdx.x == 0) a.part[(int64_t)l * a.nblk_x + blockIdx.x] = tot;
+    }
+}
+
+// ---------------------------------------------------------------- gridding
+template <typename R, int NC, int MODE, bool KAHAN>
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a) {
+    typedef Cx<R> CT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = a.g.tx, TY = a.g.ty;
+    const int cells = TX * TY;
+    CT* acc = reinterpret_cast<CT*>(smem_raw);             // [GRID_WARPS][cells]
+    CT* cmp = acc + (size_t)GRID_WARPS * cells;            // [GRID_WARPS][cells] (KAHAN)
+    const int l = blockIdx.y;
+    const int t = blockIdx.x;
+    const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
+    const int ty0 = tyi * TY, tx0 = txi * TX;
+    const int Kx = a.g.Kx, Ky = a.g.Ky;
+    for (int k = threadIdx.x; k < GRID_WARPS * cells; k += blockDim.x) {
+        acc[k] = cx<R>(0, 0);
+        if (KAHAN) cmp[k] = cx<R>(0, 0);
+    }
+    __syncthreads();
+    const int64_t tix = (int64_t)l * a.g.ntx * a.g.nty + t;
+    const int64_t e0 = a.tile_off[tix], e1 = a.tile_off[tix + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = lane >> 4, sub = lane & 15;
+    R c[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - (sub & 7)) * NC + k];
+    CT* mine = acc + (size_t)w * cells;
+    CT* mcmp = cmp + (size_t)w * cells;
+    const int cc = lane & 7, r0 = lane >> 3;
+    for (int64_t e = e0 + 2 * w; e < e1; e += 2 * GRID_WARPS) {
+        const int64_t em = e + half;
+        const bool valid = em < e1;
+        const int64_t i = a.tile_ent[valid ? em : e];
+        int cxv, cyv;
+        R fx, fy;
+        VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+        const int k0x = (cxv - 3) & (Kx - 1);
+        const int k0y = (cyv - 3) & (Ky - 1);
+        CT val;
+        if (MODE == GIN_CALLER) {
+            val = a.in[a.perm[i]];
+        } else if (MODE == GIN_SORTED) {
+            val = a.in[i];
+        } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho)
+            val = cscale(a.d[i], a.scale[l]);
+            if (a.u) val = cscale(val, sqrt(a.u[i]));
+            const bool home = (k0x / TX == txi) && (k0y / TY == tyi);
+            if (home && valid && sub == 0) a.v[i] = val;
+        }
+        if (a.w) val = cscale(val, a.w[i]);
+        const R phi = horner<R, NC>(c, (R)2 * (sub < 8 ? fx : fy) - (R)1);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int src = hh * 16;
+            const int bx = __shfl_sync(0xffffffffu, k0x, src);
+            const int by = __shfl_sync(0xffffffffu, k0y, src);
+            const int bv = __shfl_sync(0xffffffffu, (int)valid, src);
+            CT vv;
+            vv.x = __shfl_sync(0xffffffffu, val.x, src);
+            vv.y = __shfl_sync(0xffffffffu, val.y, src);
+            const R pu = __shfl_sync(0xffffffffu, phi, src + cc);
+            const R pv0 = __shfl_sync(0xffffffffu, phi, src + 8 + r0);
+            const R pv1 = __shfl_sync(0xffffffffu, phi, src + 12 + r0);
+            if (!bv) continue;
+            const int gx = ((bx + cc) & (Kx - 1)) - tx0;
+            if (gx < 0 || gx >= TX) continue;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int gy = ((by + r0 + 4 * q) & (Ky - 1)) - ty0;
+                if (gy < 0 || gy >= TY) continue;
+                const R wgt = pu * (q ? pv1 : pv0);
+                const int cell = gy * TX + gx;
+                if (KAHAN) {
+                    CT s = mine[cell], k = mcmp[cell];
+                    const R yr = fma(wgt, vv.x, -k.x), yi = fma(wgt, vv.y, -k.y);
+                    const R tr = s.x + yr, ti = s.y + yi;
+                    k.x = (tr - s.x) - yr;
+                    k.y = (ti - s.y) - yi;
+                    s.x = tr;
+                    s.y = ti;
+                    mine[cell] = s;
+                    mcmp[cell] = k;
+                } else {
+                    CT s = mine[cell];
+                    s.x = fma(wgt, vv.x, s.x);
+                    s.y = fma(wgt, vv.y, s.y);
+                    mine[cell] = s;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    CT* Gout = a.grid_out + (int64_t)l * Ky * Kx;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        CT s = acc[k];
+        if (KAHAN) {
+            // compensated combine of the per-warp (sum - compensation) values
+            R sr = s.x, si = s.y, er = -cmp[k].x, ei = -cmp[k].y;
+#pragma unroll
+            for (int ww = 1; ww < GRID_WARPS; ++ww) {
+                const CT x = acc[(size_t)ww * cells + k];
+                const CT y = cmp[(size_t)ww * cells + k];
+                R tr = sr + x.x;
+                er += (sr - tr) + x.x - y.x;
+                sr = tr;
+                R ti = si + x.y;
+                ei += (si - ti) + x.y - y.y;
+                si = ti;
+            }
+            s.x = sr + er;
+            s.y = si + ei;
+        } else {
+#pragma unroll
+            for (int ww = 1; ww < GRID_WARPS; ++ww) s = cadd(s, acc[(size_t)ww * cells + k]);
+        }
+        const int gy = k / TX, gx = k - gy * TX;
+        Gout[(int64_t)(ty0 + gy) * Kx + tx0 + gx] = s;
+    }
+}
+
+// ---------------------------------------------------------------- launches
+int degrid_blocks_x(const Plan* p) { return (p->Mmax + DEGRID_CHUNK - 1) / DEGRID_CHUNK; }
+
+template <typename R> static NufftK<R> base_args(Plan* p) {
+    NufftK<R> k{};
+    k.g = p->g;
+    k.grid = (const Cx<R>*)p->grid;
+    k.grid_out = (Cx<R>*)p->grid;
+    k.coords = p->coords;
+    k.off = p->off_d;
+    k.w = (const R*)p->w_sorted;
+    k.u = (const R*)p->u_sorted;
+    k.perm = p->perm;
+    k.kbc = (const R*)p->kbc;
+    k.tile_off = p->tile_off;
+    k.tile_ent = p->tile_ent;
+    k.nblk_x = degrid_blocks_x(p);
+    return k;
+}
+
+template <typename R, int NC>
+static hs_status degrid_t(Plan* p, const DegridArgs& da, cudaStream_t s) {
+    NufftK<R> k = base_args<R>(p);
+    k.out = (Cx<R>*)da.out;
+    k.v = (Cx<R>*)da.v;
+    k.y = (const Cx<R>*)da.y;
+    k.d = (Cx<R>*)da.d;
+    k.part = da.part;
+    if (k.nblk_x == 0 || p->g.L == 0) return HS_OK;
+    dim3 grd(k.nblk_x, p->g.L);
+    switch (da.mode) {
+        case DOUT_CALLER: k_degrid<R, NC, DOUT_CALLER><<<grd, 256, 0, s>>>(k); break;
+        case DOUT_SORTED: k_degrid<R, NC, DOUT_SORTED><<<grd, 256, 0, s>>>(k); break;
+        case DOUT_SORTED_U: k_degrid<R, NC, DOUT_SORTED_U><<<grd, 256, 0, s>>>(k); break;
+        case DOUT_PD: k_degrid<R, NC, DOUT_PD><<<grd, 256, 0, s>>>(k); break;
+        default: return fail(HS_ERR_ARG, "degrid: bad mode");
+    }
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s) {
+    if (p->prec == HS_F32) return degrid_t<float, KB_TERMS_F32>(p, a, s);
+    return degrid_t<double, KB_TERMS_F64>(p, a, s);
+}
+
+template <typename R, int NC, int MODE, bool KAHAN>
+static hs_status grid_launch(Plan* p, NufftK<R>& k, cudaStream_t s) {
+    const size_t smem = (size_t)GRID_WARPS * p->g.tx * p->g.ty * sizeof(Cx<R>) * (KAHAN ? 2 : 1);
+    dim3 grd((unsigned)p->ntiles(), p->g.L);
+    k_grid<R, NC, MODE, KAHAN><<<grd, GRID_WARPS * 32, smem, s>>>(k);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+template <typename R, int NC, int MODE, bool KAHAN> static hs_status grid_attr() {
+    const int smem = GRID_WARPS * GRID_TILE * GRID_TILE * (int)sizeof(Cx<R>) * (KAHAN ? 2 : 1);
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_grid<R, NC, MODE, KAHAN>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return HS_OK;
+}
+
+// Opt the gridding kernels into their dynamic shared memory (once per process).
+hs_status nufft_init() {
+    static bool done = false;
+    if (done) return HS_OK;
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_CALLER, false>()));
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_SORTED, false>()));
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_PD, false>()));
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_CALLER, true>()));
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_SORTED, true>()));
+    HS_TRY((grid_attr<float, KB_TERMS_F32, GIN_PD, true>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_CALLER, false>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_SORTED, false>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_PD, false>()));
+    done = true;
+    return HS_OK;
+}
+
+template <typename R, int NC, bool KAHAN>
+static hs_status grid_t(Plan* p, const GridArgs& ga, cudaStream_t s) {
+    NufftK<R> k = base_args<R>(p);
+    k.in = (const Cx<R>*)ga.in;
+    k.d = (Cx<R>*)ga.d;
+    k.scale = (const R*)ga.scale;
+    k.v = (Cx<R>*)ga.v;
+    if (p->g.L == 0) return HS_OK;
+    switch (ga.mode) {
+        case GIN_CALLER: return grid_launch<R, NC, GIN_CALLER, KAHAN>(p, k, s);
+        case GIN_SORTED: return grid_launch<R, NC, GIN_SORTED, KAHAN>(p, k, s);
+        case GIN_PD: return grid_launch<R, NC, GIN_PD, KAHAN>(p, k, s);
+        default: return fail(HS_ERR_ARG, "grid: bad mode");
+    }
+}
+
+hs_status grid(Plan* p, const GridArgs& a, cudaStream_t s) {
+    if (p->prec == HS_F32) {
+        if (p->flags & HS_PLAN_COMPENSATED) return grid_t<float, KB_TERMS_F32, true>(p, a, s);
+        return grid_t<float, KB_TERMS_F32, false>(p, a, s);
+    }
+    return grid_t<double, KB_TERMS_F64, false>(p, a, s);
+}
+
+}  // namespace hs

@@ -1,0 +1,331 @@
+// Plan construction: everything the operators derive from the uv coverage.
+//
+//  * grid coordinates t = u K / (2 pi) per axis, split into the cell floor(t)
+//    (mod K) and the fraction; FP32 plans store both in one 32-bit fixed-point
+//    word per axis (fraction resolution 2^-23 .. 2^-20 cells, computed in FP64
+//    so the FP32 kernels never form t themselves), FP64 plans store the exact
+//    FP64 fraction;
+//  * a per-channel sort of the visibilities by the 32 x 32 grid tile holding
+//    the start of their 8 x 8 window, then by cell, so that consecutive
+//    visibilities touch neighbouring grid cells;
+//  * for every (channel, tile) the list of visibilities whose window overlaps
+//    the tile (a window straddles at most 2 x 2 tiles), which the gridding
+//    kernel consumes without atomics;
+//  * the Kaiser-Bessel polynomial pieces, the Z scaling, the FFT twiddles;
+//  * all scratch buffers, so that no compute call allocates.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+hs_status dwt_init();
+hs_status fft_init();
+hs_status nufft_init();
+hs_status prox_init();
+int64_t gram_part_doubles(int L);
+
+hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return HS_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(HS_ERR_NOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    p->allocs.push_back(*ptr);
+    p->device_bytes += (int64_t)bytes;
+    return HS_OK;
+}
+
+void plan_free(Plan* p) {
+    for (void* q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+}
+
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+template <typename T> static hs_status upload(Plan* p, void** dst, const std::vector<T>& h) {
+    HS_TRY(plan_alloc(p, dst, h.size() * sizeof(T)));
+    if (!h.empty()) HS_CHECK_CUDA(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HS_OK;
+}
+
+template <typename R>
+static hs_status upload_real(Plan* p, void** dst, const std::vector<double>& h) {
+    std::vector<R> v(h.size());
+    for (size_t i = 0; i < h.size(); ++i) v[i] = (R)h[i];
+    return upload(p, dst, v);
+}
+
+static hs_status download_real(const Plan* p, const void* src, int64_t n, std::vector<double>& out,
+                               cudaStream_t s) {
+    out.assign((size_t)n, 0.0);
+    if (n == 0) return HS_OK;
+    if (p->prec == HS_F32) {
+        std::vector<float> tmp((size_t)n);
+        HS_CHECK_CUDA(cudaMemcpyAsync(tmp.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+        HS_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < n; ++i) out[i] = tmp[i];
+    } else {
+        HS_CHECK_CUDA(cudaMemcpyAsync(out.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    return HS_OK;
+}
+
+static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, const void* weights,
+                       const void* precond, cudaStream_t s) {
+    Geo& g = p->g;
+    const int L = g.L;
+    p->off_h.assign(vis_offsets, vis_offsets + L + 1);
+    if (p->off_h[0] != 0) return fail(HS_ERR_ARG, "vis_offsets[0] must be 0");
+    int64_t Mmax = 0;
+    for (int l = 0; l < L; ++l) {
+        const int64_t m = p->off_h[l + 1] - p->off_h[l];
+        if (m < 0) return fail(HS_ERR_ARG, "vis_offsets must be nondecreasing (channel %d)", l);
+        Mmax = std::max(Mmax, m);
+    }
+    const int64_t M = p->off_h[L];
+    if (M >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "total visibilities must be < 2^31");
+    if (M > 0 && uv == nullptr) return fail(HS_ERR_ARG, "uv is null");
+    p->M_total = M;
+    p->Mmax = (int)Mmax;
+
+    std::vector<double> uvh, wh, uh;
+    HS_TRY(download_real(p, uv, 2 * M, uvh, s));
+    if (weights) HS_TRY(download_real(p, weights, M, wh, s));
+    if (precond) HS_TRY(download_real(p, precond, M, uh, s));
+    for (int64_t i = 0; i < 2 * M; ++i) {
+        const double v = uvh[i];
+        if (!std::isfinite(v) || v < -M_PI || v >= M_PI)
+            return fail(HS_ERR_ARG, "uv[%lld] = %g outside [-pi, pi)", (long long)(i / 2), v);
+    }
+    for (int64_t i = 0; i < (int64_t)uh.size(); ++i)
+        if (!(uh[i] > 0.0) || !std::isfinite(uh[i]))
+            return fail(HS_ERR_ARG, "precond[%lld] must be finite and > 0", (long long)i);
+
+    const int Kx = g.Kx, Ky = g.Ky, TX = g.tx, TY = g.ty;
+    // per-visibility cells and fractions (FP64, same expression as t = u K / (2 pi))
+    std::vector<int> cellx(M), celly(M);
+    std::vector<double> fx(M), fy(M);
+    for (int64_t i = 0; i < M; ++i) {
+        const double tu = uvh[2 * i] * Kx / (2.0 * M_PI);
+        const double tv = uvh[2 * i + 1] * Ky / (2.0 * M_PI);
+        const double flu = std::floor(tu), flv = std::floor(tv);
+        fx[i] = tu - flu;
+        fy[i] = tv - flv;
+        cellx[i] = (int)((((int64_t)flu % Kx) + Kx) % Kx);
+        celly[i] = (int)((((int64_t)flv % Ky) + Ky) % Ky);
+    }
+    // sort each channel by (tile of the window start, cell)
+    std::vector<int> perm(M);
+    std::vector<uint64_t> keys;
+    for (int l = 0; l < L; ++l) {
+        const int64_t a = p->off_h[l], b = p->off_h[l + 1];
+        keys.resize(b - a);
+        for (int64_t i = a; i < b; ++i) {
+            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+            const uint64_t tile = (uint64_t)(k0y / TY) * g.ntx + (uint64_t)(k0x / TX);
+            const uint64_t key = (tile * TY + (uint64_t)(k0y % TY)) * TX + (uint64_t)(k0x % TX);
+            keys[i - a] = (key << 32) | (uint64_t)(i - a);
+        }
+        std::sort(keys.begin(), keys.end());
+        for (int64_t r = 0; r < b - a; ++r) perm[a + r] = (int)(a + (int64_t)(keys[r] & 0xffffffffu));
+    }
+    HS_TRY(upload(p, (void**)&p->perm, perm));
+
+    if (p->prec == HS_F32) {
+        std::vector<uint32_t> c((size_t)2 * M);
+        for (int64_t r = 0; r < M; ++r) {
+            const int64_t i = perm[r];
+            int cxv = cellx[i], cyv = celly[i];
+            uint64_t qx = (uint64_t)std::llround(std::ldexp(fx[i], g.fbx));
+            uint64_t qy = (uint64_t)std::llround(std::ldexp(fy[i], g.fby));
+            if (qx >= (1ull << g.fbx)) {
+                qx = 0;
+                cxv = (cxv + 1) & (Kx - 1);
+            }
+            if (qy >= (1ull << g.fby)) {
+                qy = 0;
+                cyv = (cyv + 1) & (Ky - 1);
+            }
+            c[2 * r] = ((uint32_t)cxv << g.fbx) | (uint32_t)qx;
+            c[2 * r + 1] = ((uint32_t)cyv << g.fby) | (uint32_t)qy;
+            cellx[i] = cxv;   // tile membership below uses the stored cell
+            celly[i] = cyv;
+        }
+        HS_TRY(upload(p, &p->coords, c));
+    } else {
+        std::vector<Coord64> c(M);
+        for (int64_t r = 0; r < M; ++r) {
+            const int64_t i = perm[r];
+            c[r].fx = fx[i];
+            c[r].fy = fy[i];
+            c[r].cx = cellx[i];
+            c[r].cy = celly[i];
+        }
+        HS_TRY(upload(p, &p->coords, c));
+    }
+    if (!wh.empty()) {
+        std::vector<double> ws(M);
+        for (int64_t r = 0; r < M; ++r) ws[r] = wh[perm[r]];
+        HS_TRY(p->prec == HS_F32 ? upload_real<float>(p, &p->w_sorted, ws)
+                                 : upload_real<double>(p, &p->w_sorted, ws));
+    }
+    if (!uh.empty()) {
+        std::vector<double> us(M);
+        for (int64_t r = 0; r < M; ++r) us[r] = uh[perm[r]];
+        HS_TRY(p->prec == HS_F32 ? upload_real<float>(p, &p->u_sorted, us)
+                                 : upload_real<double>(p, &p->u_sorted, us));
+    }
+
+    // gridding lists: every (channel, tile) overlapped by a window
+    const int64_t nt = p->ntiles();
+    std::vector<int64_t> toff((size_t)L * nt + 1, 0);
+    auto tiles_of = [&](int64_t r, int* txs, int* tys, int& ntx_, int& nty_) {
+        const int64_t i = perm[r];
+        const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+        txs[0] = k0x / TX;
+        txs[1] = ((k0x + 7) & (Kx - 1)) / TX;
+        tys[0] = k0y / TY;
+        tys[1] = ((k0y + 7) & (Ky - 1)) / TY;
+        ntx_ = txs[1] != txs[0] ? 2 : 1;
+        nty_ = tys[1] != tys[0] ? 2 : 1;
+    };
+    for (int l = 0; l < L; ++l)
+        for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
+            int txs[2], tys[2], a, b;
+            tiles_of(r, txs, tys, a, b);
+            for (int yy = 0; yy < b; ++yy)
+                for (int xx = 0; xx < a; ++xx) ++toff[1 + (size_t)l * nt + tys[yy] * g.ntx + txs[xx]];
+        }
+    for (size_t k = 1; k < toff.size(); ++k) toff[k] += toff[k - 1];
+    p->n_ent = toff.back();
+    std::vector<int> ent((size_t)p->n_ent);
+    {
+        std::vector<int64_t> fill(toff.begin(), toff.end() - 1);
+        for (int l = 0; l < L; ++l)
+            for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
+                int txs[2], tys[2], a, b;
+                tiles_of(r, txs, tys, a, b);
+                for (int yy = 0; yy < b; ++yy)
+                    for (int xx = 0; xx < a; ++xx)
+                        ent[fill[(size_t)l * nt + tys[yy] * g.ntx + txs[xx]]++] = (int)r;
+            }
+    }
+    HS_TRY(upload(p, (void**)&p->tile_off, toff));
+    HS_TRY(upload(p, (void**)&p->tile_ent, ent));
+    HS_TRY(upload(p, (void**)&p->off_d, p->off_h));
+
+    // tables
+    std::vector<double> kbc;
+    p->kb_terms = p->prec == HS_F32 ? KB_TERMS_F32 : KB_TERMS_F64;
+    p->kb_fit_err = kb_poly_fit(p->J, p->beta, p->kb_terms, &kbc);
+    std::vector<double> cx(g.nx), cy(g.ny);
+    for (int i = 0; i < g.nx; ++i) cx[i] = 1.0 / kb_phihat((double)(i - g.nx / 2) / Kx, p->J, p->beta);
+    for (int i = 0; i < g.ny; ++i) cy[i] = 1.0 / kb_phihat((double)(i - g.ny / 2) / Ky, p->J, p->beta);
+    std::vector<double> twx(2 * (size_t)Kx), twy(2 * (size_t)Ky);
+    for (int m = 0; m < Kx; ++m) {
+        twx[2 * m] = std::cos(2.0 * M_PI * m / Kx);
+        twx[2 * m + 1] = -std::sin(2.0 * M_PI * m / Kx);
+    }
+    for (int m = 0; m < Ky; ++m) {
+        twy[2 * m] = std::cos(2.0 * M_PI * m / Ky);
+        twy[2 * m + 1] = -std::sin(2.0 * M_PI * m / Ky);
+    }
+    if (p->prec == HS_F32) {
+        HS_TRY(upload_real<float>(p, &p->kbc, kbc));
+        HS_TRY(upload_real<float>(p, &p->cxs, cx));
+        HS_TRY(upload_real<float>(p, &p->cys, cy));
+        HS_TRY(upload_real<float>(p, &p->twx, twx));
+        HS_TRY(upload_real<float>(p, &p->twy, twy));
+    } else {
+        HS_TRY(upload_real<double>(p, &p->kbc, kbc));
+        HS_TRY(upload_real<double>(p, &p->cxs, cx));
+        HS_TRY(upload_real<double>(p, &p->cys, cy));
+        HS_TRY(upload_real<double>(p, &p->twx, twx));
+        HS_TRY(upload_real<double>(p, &p->twy, twy));
+    }
+
+    // scratch
+    const size_t rs = p->rsize(), cs = p->csize();
+    const int64_t N = p->N();
+    HS_TRY(plan_alloc(p, &p->grid, (size_t)L * Ky * Kx * cs));
+    HS_TRY(plan_alloc(p, &p->tmp, (size_t)L * g.ny * Kx * cs));
+    HS_TRY(plan_alloc(p, &p->vis, (size_t)std::max<int64_t>(M, 1) * cs));
+    HS_TRY(plan_alloc(p, &p->dwt_a, (size_t)NW * L * N * rs));
+    HS_TRY(plan_alloc(p, &p->dwt_b, (size_t)NW * L * N * rs));
+    HS_TRY(plan_alloc(p, &p->xbuf, (size_t)L * N * rs));
+    HS_TRY(plan_alloc(p, &p->xbuf2, (size_t)L * N * rs));
+    const int64_t nbx = (Mmax + DEGRID_CHUNK - 1) / DEGRID_CHUNK;
+    p->part_n = std::max<int64_t>({(int64_t)L * std::max<int64_t>(nbx, 1),
+                                   gram_part_doubles(std::min(L, MAX_L_NUC)), 8192});
+    HS_TRY(plan_alloc(p, (void**)&p->part, (size_t)p->part_n * sizeof(double)));
+    HS_TRY(plan_alloc(p, (void**)&p->gram, sizeof(double) * MAX_L_NUC * MAX_L_NUC));
+    HS_TRY(plan_alloc(p, (void**)&p->eigf, sizeof(double) * MAX_L_NUC * MAX_L_NUC));
+    HS_TRY(plan_alloc(p, (void**)&p->sv, sizeof(double) * MAX_L_NUC));
+    HS_TRY(plan_alloc(p, (void**)&p->dscal, sizeof(double) * 6 * std::max(L, 1)));
+    return HS_OK;
+}
+
+hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, const void* uv,
+                      const void* weights, const void* precond, int oversample, int J, double kb_beta,
+                      int levels, hs_prec prec, unsigned flags, cudaStream_t s) {
+    if (out == nullptr) return fail(HS_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (vis_offsets == nullptr) return fail(HS_ERR_ARG, "vis_offsets is null");
+    if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 8192 || ny > 8192)
+        return fail(HS_ERR_ARG, "nx, ny must be powers of two in [16, 8192] (got %d x %d)", nx, ny);
+    if (L < 1 || L > 1024) return fail(HS_ERR_ARG, "L must be in [1, 1024] (got %d)", L);
+    if (oversample != 2) return fail(HS_ERR_ARG, "oversample must be 2 (got %d)", oversample);
+    if (J != 8) return fail(HS_ERR_ARG, "J must be 8 (got %d)", J);
+    if (levels < 1 || levels > 8 || (nx >> levels) < 1 || (ny >> levels) < 1 ||
+        nx % (1 << levels) || ny % (1 << levels))
+        return fail(HS_ERR_ARG, "wavelet_levels %d incompatible with %d x %d", levels, nx, ny);
+    if (prec != HS_F32 && prec != HS_F64) return fail(HS_ERR_ARG, "bad precision %d", (int)prec);
+    if (flags & ~(unsigned)HS_PLAN_COMPENSATED) return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
+    HS_TRY(dwt_init());
+    HS_TRY(fft_init());
+    HS_TRY(nufft_init());
+    HS_TRY(prox_init());
+    std::unique_ptr<Plan> p(new Plan());
+    p->prec = prec;
+    p->flags = flags;
+    p->levels = levels;
+    p->J = J;
+    p->o = oversample;
+    p->beta = kb_beta > 0 ? kb_beta
+                          : M_PI * std::sqrt((double)(J * J) / (oversample * oversample) *
+                                                 (oversample - 0.5) * (oversample - 0.5) - 0.8);
+    Geo& g = p->g;
+    g.nx = nx;
+    g.ny = ny;
+    g.L = L;
+    g.Kx = oversample * nx;
+    g.Ky = oversample * ny;
+    g.fbx = std::min(23, 32 - ilog2(g.Kx));
+    g.fby = std::min(23, 32 - ilog2(g.Ky));
+    g.tx = std::min(GRID_TILE, g.Kx);
+    g.ty = std::min(GRID_TILE, g.Ky);
+    g.ntx = g.Kx / g.tx;
+    g.nty = g.Ky / g.ty;
+    hs_status st = build(p.get(), vis_offsets, uv, weights, precond, s);
+    if (st != HS_OK) {
+        plan_free(p.get());
+        return st;
+    }
+    *out = p.release();
+    return HS_OK;
+}
+
+}  // namespace hs

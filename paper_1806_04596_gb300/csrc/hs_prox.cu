@@ -1,0 +1,618 @@
+// Proximity operators of Sec. 3.3 and the primal update of Algorithm 2.
+//
+//  l2,1      rows (basis, pixel) across the L channels (Eq. "prox-L21"), with
+//            the Moreau dual form a min(1, lambda / ||a||) used in step 7.
+//  l2 ball   per-channel projection onto B(y_l, eps_l) (functions g_l), norms
+//            accumulated in FP64 as deterministic per-CTA partial sums.
+//  nuclear   Eq. "prox-L*" through the L x L Gram matrix S = Z^T Z (per-tile
+//            products, FP64 combine), a cyclic Jacobi eigendecomposition of S in
+//            FP64 in one CTA (round-robin parallel ordering), and the apply
+//            Z V diag(f) V^T with f the per-singular-value factor.
+//  primal    steps 20-23: G = k1 P + k2 A~ + k3 Phi^dagger v, X = P_+(X - tau G),
+//            X~ = 2 X - X_prev, beta partial sums.
+#include <cmath>
+
+#include "hs_device.cuh"
+#include "hs_internal.h"
+
+namespace hs {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- reductions
+// out[c] = sum_b part[c * nb + b] for c < nc, one block per c, fixed order.
+__global__ void k_reduce_rows(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)c * nb + b];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[c] = s;
+}
+
+// ---------------------------------------------------------------- l2,1
+template <typename R>
+__global__ void k_l21(const R* __restrict__ A, const R* __restrict__ W, const R* __restrict__ w_rows,
+                      R thr, int dual, R* __restrict__ out, int L, int64_t N) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NB * N) return;
+    const int b = (int)(t / N);
+    const int64_t pix = t - (int64_t)b * N;
+    const int64_t base = (int64_t)b * L * N + pix;
+    R s = 0;
+    for (int l = 0; l < L; ++l) {
+        R q = A[base + (int64_t)l * N];
+        if (W) q += W[base + (int64_t)l * N];
+        s = fma(q, q, s);
+    }
+    const R nrm = sqrt(s);
+    const R lam = thr * (w_rows ? w_rows[t] : (R)1);
+    R f;
+    if (dual) f = (nrm > lam) ? lam / nrm : (R)1;
+    else f = (nrm > lam) ? (nrm - lam) / nrm : (R)0;
+    for (int l = 0; l < L; ++l) {
+        R q = A[base + (int64_t)l * N];
+        if (W) q += W[base + (int64_t)l * N];
+        out[base + (int64_t)l * N] = q * f;
+    }
+}
+
+template <typename R>
+__global__ void k_l21_norm(const R* __restrict__ A, const R* __restrict__ w_rows, int L, int64_t N,
+                           double* __restrict__ part) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)NB * N;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / N);
+        const int64_t pix = t - (int64_t)b * N;
+        const int64_t base = (int64_t)b * L * N + pix;
+        double s = 0.0;
+        for (int l = 0; l < L; ++l) {
+            const double q = (double)A[base + (int64_t)l * N];
+            s += q * q;
+        }
+        acc += sqrt(s) * (w_rows ? (double)w_rows[t] : 1.0);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows, double thr,
+                    int dual, void* out, cudaStream_t s) {
+    const int64_t N = p->N();
+    const unsigned g = nblk((int64_t)NB * N, 256);
+    if (p->prec == HS_F32)
+        k_l21<float><<<g, 256, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
+                                       (float)thr, dual, (float*)out, p->g.L, N);
+    else
+        k_l21<double><<<g, 256, 0, s>>>((const double*)A, (const double*)Wadd,
+                                        (const double*)w_rows, thr, dual, (double*)out, p->g.L, N);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status l21_norm(Plan* p, const void* A, const void* w_rows, double* out_dev, cudaStream_t s) {
+    const int64_t N = p->N();
+    const int nb = 512;
+    if (p->prec == HS_F32)
+        k_l21_norm<float><<<nb, 256, 0, s>>>((const float*)A, (const float*)w_rows, p->g.L, N, p->part);
+    else
+        k_l21_norm<double><<<nb, 256, 0, s>>>((const double*)A, (const double*)w_rows, p->g.L, N,
+                                              p->part);
+    HS_CHECK_LAUNCH();
+    k_reduce_rows<<<1, 256, 0, s>>>(p->part, nb, out_dev);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------- l2 ball
+// Per-CTA partial ||z - y||^2 over [off[l] + bx * CH, ...), grid (nbx, L).
+template <typename R>
+__global__ void k_ball_norm(const Cx<R>* __restrict__ Z, const Cx<R>* __restrict__ Y,
+                            const int64_t* __restrict__ off, int nbx, double* __restrict__ part) {
+    __shared__ double red[32];
+    const int l = blockIdx.y;
+    const int64_t beg = off[l] + (int64_t)blockIdx.x * DEGRID_CHUNK;
+    const int64_t end = min(off[l + 1], beg + DEGRID_CHUNK);
+    double s = 0.0;
+    for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const Cx<R> d = csub(Z[i], Y[i]);
+        s += (double)d.x * d.x + (double)d.y * d.y;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(int64_t)l * nbx + blockIdx.x] = s;
+}
+
+// rho_l = sqrt(sum of partials); scale_l = max(0, 1 - eps_l / rho_l) (0 when rho = 0).
+template <typename R>
+__global__ void k_ball_scale(const double* __restrict__ part, int nb, const double* __restrict__ eps,
+                             double* __restrict__ rho, R* __restrict__ scale) {
+    __shared__ double red[32];
+    const int l = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)l * nb + b];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        const double r = sqrt(s);
+        if (rho) rho[l] = r;
+        const double e = eps[l];
+        scale[l] = (R)((r > e) ? (1.0 - e / r) : 0.0);
+    }
+}
+
+template <typename R>
+__global__ void k_ball_apply(const Cx<R>* __restrict__ Z, const Cx<R>* __restrict__ Y,
+                             const int64_t* __restrict__ off, int L, const R* __restrict__ scale,
+                             int dual, Cx<R>* __restrict__ out, int64_t total) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = L;   // channel: off[lo] <= i < off[lo+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const R sc = scale[lo];
+        const Cx<R> d = csub(Z[i], Y[i]);
+        // (z - y) * max(0, 1 - eps/rho) is z - P_B(z); P_B(z) = z - that
+        const Cx<R> r = cscale(d, sc);
+        out[i] = dual ? r : csub(Z[i], r);
+    }
+}
+
+hs_status ball_scale_from_partials(Plan* p, const double* part, int nparts, const double* eps,
+                                   double* rho, void* scale_real, cudaStream_t s) {
+    if (p->prec == HS_F32)
+        k_ball_scale<float><<<p->g.L, 256, 0, s>>>(part, nparts, eps, rho, (float*)scale_real);
+    else
+        k_ball_scale<double><<<p->g.L, 256, 0, s>>>(part, nparts, eps, rho, (double*)scale_real);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status ball_project(Plan* p, const void* Z, const void* Yd, const double* eps, int dual,
+                       void* out, double* rho_out, cudaStream_t s) {
+    const int nbx = degrid_blocks_x(p);
+    const int L = p->g.L;
+    if (L == 0 || p->M_total == 0) {
+        if (rho_out && L) HS_CHECK_CUDA(cudaMemsetAsync(rho_out, 0, sizeof(double) * L, s));
+        return HS_OK;
+    }
+    dim3 g(nbx, L);
+    void* scale = p->dscal + 2 * L;   // L reals (fits in 2 L doubles)
+    if (p->prec == HS_F32) {
+        k_ball_norm<float><<<g, 256, 0, s>>>((const float2*)Z, (const float2*)Yd, p->off_d, nbx, p->part);
+        HS_CHECK_LAUNCH();
+        k_ball_scale<float><<<L, 256, 0, s>>>(p->part, nbx, eps, rho_out, (float*)scale);
+        HS_CHECK_LAUNCH();
+        k_ball_apply<float><<<nblk(p->M_total, 256) > 8192 ? 8192 : nblk(p->M_total, 256), 256, 0, s>>>(
+            (const float2*)Z, (const float2*)Yd, p->off_d, L, (const float*)scale, dual, (float2*)out,
+            p->M_total);
+    } else {
+        k_ball_norm<double><<<g, 256, 0, s>>>((const double2*)Z, (const double2*)Yd, p->off_d, nbx,
+                                              p->part);
+        HS_CHECK_LAUNCH();
+        k_ball_scale<double><<<L, 256, 0, s>>>(p->part, nbx, eps, rho_out, (double*)scale);
+        HS_CHECK_LAUNCH();
+        k_ball_apply<double><<<nblk(p->M_total, 256) > 8192 ? 8192 : nblk(p->M_total, 256), 256, 0, s>>>(
+            (const double2*)Z, (const double2*)Yd, p->off_d, L, (const double*)scale, dual,
+            (double2*)out, p->M_total);
+    }
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------- nuclear norm
+constexpr int GRAM_ROWS = 32;     // pixels per shared-memory tile (R sums, then FP64)
+constexpr int GRAM_CTAS = 304;    // 2 per SM
+constexpr int GRAM_PER = 9;       // upper-triangle entries per thread (256 threads, L <= 64)
+
+// Partial Gram matrices: CTA c accumulates sum over its pixel tiles of z z^T for
+// the upper triangle (i <= j), tile sums in R, running sum in FP64.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gram(const R* __restrict__ X, const R* __restrict__ Xa,
+                                              int L, int64_t N, double* __restrict__ part) {
+    __shared__ R zs[GRAM_ROWS][MAX_L_NUC + 1];
+    const int P = L * (L + 1) / 2;
+    int pi[GRAM_PER], pj[GRAM_PER];
+    double acc[GRAM_PER];
+#pragma unroll
+    for (int q = 0; q < GRAM_PER; ++q) {
+        const int e = threadIdx.x + q * 256;
+        acc[q] = 0.0;
+        pi[q] = 0;
+        pj[q] = 0;
+        if (e < P) {   // unrank e -> (i, j), i <= j, row-major over the upper triangle
+            int i = 0, rem = e;
+            while (rem >= L - i) {
+                rem -= L - i;
+                ++i;
+            }
+            pi[q] = i;
+            pj[q] = i + rem;
+        }
+    }
+    const int64_t ntile = (N + GRAM_ROWS - 1) / GRAM_ROWS;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t n0 = tile * GRAM_ROWS;
+        __syncthreads();
+        for (int k = threadIdx.x; k < GRAM_ROWS * L; k += 256) {
+            const int l = k / GRAM_ROWS, r = k - l * GRAM_ROWS;
+            const int64_t n = n0 + r;
+            R z = 0;
+            if (n < N) {
+                z = X[(int64_t)l * N + n];
+                if (Xa) z += Xa[(int64_t)l * N + n];
+            }
+            zs[r][l] = z;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GRAM_PER; ++q) {
+            if (threadIdx.x + q * 256 < P) {
+                R s = 0;
+                const int i = pi[q], j = pj[q];
+#pragma unroll 8
+                for (int r = 0; r < GRAM_ROWS; ++r) s = fma(zs[r][i], zs[r][j], s);
+                acc[q] += (double)s;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < GRAM_PER; ++q) {
+        const int e = threadIdx.x + q * 256;
+        if (e < P) part[(int64_t)e * gridDim.x + blockIdx.x] = acc[q];
+    }
+}
+
+// Sum the per-CTA partials (fixed order) and expand to the full symmetric matrix.
+__global__ void k_gram_reduce(const double* __restrict__ part, int nb, int L, double* __restrict__ S) {
+    __shared__ double red[32];
+    const int e = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)e * nb + b];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        int i = 0, rem = e;
+        while (rem >= L - i) {
+            rem -= L - i;
+            ++i;
+        }
+        const int j = i + rem;
+        S[i * L + j] = s;
+        S[j * L + i] = s;
+    }
+}
+
+// Cyclic Jacobi eigendecomposition of the symmetric L x L matrix S (FP64, one
+// CTA), parallel round-robin ordering: each round applies n/2 disjoint
+// rotations, (c, s) from the symmetric Schur decomposition of the 2 x 2 block
+// (Golub & Van Loan, Alg. 8.4.1). Then, with the eigenvalues sorted in
+// descending order, sigma_j = sqrt(max(lambda_j, 0)) and
+//   dual: f_j = min(1, thr w_j / sigma_j) (1 when sigma_j = 0)
+//   prox: f_j = max(0, 1 - thr w_j / sigma_j) (0 when sigma_j = 0),
+// and writes Mf = V diag(f) V^T (L x L) and the singular values.
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ S, int L,
+                                                 const double* __restrict__ w_sv, double thr,
+                                                 int dual, double* __restrict__ Mf,
+                                                 double* __restrict__ sv_out, int max_sweeps) {
+    constexpr int LD = MAX_L_NUC + 1;
+    extern __shared__ __align__(16) double jac_smem[];
+    double* A = jac_smem;                  // MAX_L_NUC * LD
+    double* V = jac_smem + MAX_L_NUC * LD;   // MAX_L_NUC * LD
+    __shared__ double cs[MAX_L_NUC / 2], sn[MAX_L_NUC / 2];
+    __shared__ int pp[MAX_L_NUC / 2], qq[MAX_L_NUC / 2];
+    __shared__ double red[32];
+    __shared__ double fvec[MAX_L_NUC];
+    __shared__ int order[MAX_L_NUC];
+    __shared__ int done;
+    const int n = (L + 1) & ~1;   // even size, padded with a zero row/column
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int k = tid; k < n * n; k += nt) {
+        const int i = k / n, j = k - i * n;
+        A[i * LD + j] = (i < L && j < L) ? S[i * L + j] : 0.0;
+        V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int k = tid; k < n * n; k += nt) {
+            const int i = k / n, j = k - i * n;
+            const double a = A[i * LD + j];
+            if (i == j) dia += a * a;
+            else off += a * a;
+        }
+        off = block_sum(off, red);
+        dia = block_sum(dia, red);
+        if (tid == 0) done = !(off > 1e-32 * dia) ? 1 : 0;
+        __syncthreads();
+        if (done) break;
+        for (int r = 0; r < n - 1; ++r) {
+            if (tid < n / 2) {
+                int p, q;
+                if (tid == 0) {
+                    p = r;
+                    q = n - 1;
+                } else {
+                    p = (r + tid) % (n - 1);
+                    q = (r - tid + (n - 1)) % (n - 1);
+                }
+                if (p > q) {
+                    const int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                const double apq = A[p * LD + q];
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0 &&
+                    fabs(apq) > 1e-300 + 1e-18 * sqrt(fabs(A[p * LD + p] * A[q * LD + q]))) {
+                    const double tau = (A[q * LD + q] - A[p * LD + p]) / (2.0 * apq);
+                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    s = t * c;
+                }
+                cs[tid] = c;
+                sn[tid] = s;
+                pp[tid] = p;
+                qq[tid] = q;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int k = tid; k < (n / 2) * n; k += nt) {
+                const int pr = k / n, col = k - pr * n;
+                const int p = pp[pr], q = qq[pr];
+                const double c = cs[pr], s = sn[pr];
+                const double ap = A[p * LD + col], aq = A[q * LD + col];
+                A[p * LD + col] = c * ap - s * aq;
+                A[q * LD + col] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int k = tid; k < (n / 2) * n; k += nt) {
+                const int pr = k / n, row = k - pr * n;
+                const int p = pp[pr], q = qq[pr];
+                const double c = cs[pr], s = sn[pr];
+                const double ap = A[row * LD + p], aq = A[row * LD + q];
+                A[row * LD + p] = c * ap - s * aq;
+                A[row * LD + q] = s * ap + c * aq;
+                const double vp = V[row * LD + p], vq = V[row * LD + q];
+                V[row * LD + p] = c * vp - s * vq;
+                V[row * LD + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+            if (tid < n / 2) {   // the rotated pair is now decoupled
+                const int p = pp[tid], q = qq[tid];
+                if (sn[tid] != 0.0) {
+                    A[p * LD + q] = 0.0;
+                    A[q * LD + p] = 0.0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {   // descending eigenvalue order (selection sort, L <= 64)
+        for (int i = 0; i < L; ++i) order[i] = i;
+        for (int i = 0; i < L; ++i) {
+            int best = i;
+            for (int j = i + 1; j < L; ++j)
+                if (A[order[j] * LD + order[j]] > A[order[best] * LD + order[best]]) best = j;
+            const int tmp = order[i];
+            order[i] = order[best];
+            order[best] = tmp;
+        }
+        for (int j = 0; j < L; ++j) {
+            const double lam = A[order[j] * LD + order[j]];
+            const double sig = sqrt(lam > 0.0 ? lam : 0.0);
+            const double lamb = thr * (w_sv ? w_sv[j] : 1.0);
+            double f;
+            if (dual) f = (sig > lamb) ? lamb / sig : 1.0;
+            else f = (sig > lamb) ? 1.0 - lamb / sig : 0.0;
+            fvec[j] = f;
+            if (sv_out) sv_out[j] = sig;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < L * L; k += nt) {
+        const int i = k / L, m = k - i * L;
+        double acc = 0.0;
+        for (int j = 0; j < L; ++j) acc += V[i * LD + order[j]] * fvec[j] * V[m * LD + order[j]];
+        Mf[i * L + m] = acc;
+    }
+}
+
+// out[:, m] = sum_i Z[:, i] Mf[i, m] with Z = X + Xa, one thread per pixel,
+// the pixel's L values in registers, Mf broadcast from shared memory. In FP32
+// the FP64 factor matrix is carried as two FP32 parts (hi + lo), so that its
+// rounding does not enter the result: the output is often a small remainder of
+// a large Z (the dual form keeps the small singular values).
+template <typename R, int LMAX>
+__global__ void __launch_bounds__(128) k_lowrank_apply(const R* __restrict__ X,
+                                                       const R* __restrict__ Xa,
+                                                       const double* __restrict__ Mf, int L,
+                                                       int64_t N, R* __restrict__ out) {
+    constexpr bool SPLIT = sizeof(R) == 4;
+    __shared__ R Ms[LMAX * LMAX];
+    __shared__ R Ml[SPLIT ? LMAX * LMAX : 1];
+    for (int k = threadIdx.x; k < L * L; k += blockDim.x) {
+        const double m = Mf[k];
+        Ms[k] = (R)m;
+        if (SPLIT) Ml[k] = (R)(m - (double)(R)m);
+    }
+    __syncthreads();
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    R z[LMAX];
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i) {
+        z[i] = 0;
+        if (i < L) {
+            z[i] = X[(int64_t)i * N + n];
+            if (Xa) z[i] += Xa[(int64_t)i * N + n];
+        }
+    }
+    for (int m = 0; m < L; ++m) {
+        R acc = 0, acc2 = 0;
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i)
+            if (i < L) {
+                acc = fma(z[i], Ms[i * L + m], acc);
+                if (SPLIT) acc2 = fma(z[i], Ml[i * L + m], acc2);
+            }
+        out[(int64_t)m * N + n] = acc + acc2;
+    }
+}
+
+template <typename R>
+static hs_status lowrank_apply_t(Plan* p, const void* X, const void* Xa, void* out, cudaStream_t s) {
+    const int L = p->g.L;
+    const int64_t N = p->N();
+    const unsigned g = nblk(N, 128);
+    if (L <= 8)
+        k_lowrank_apply<R, 8><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
+    else if (L <= 16)
+        k_lowrank_apply<R, 16><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
+    else if (L <= 32)
+        k_lowrank_apply<R, 32><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
+    else
+        k_lowrank_apply<R, 64><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
+                        int dual, void* out, double* sv_out, cudaStream_t s) {
+    const int L = p->g.L;
+    if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "nuclear prox: L = %d exceeds %d", L, MAX_L_NUC);
+    const int64_t N = p->N();
+    const int P = L * (L + 1) / 2;
+    double* gpart = p->part;   // P * GRAM_CTAS doubles
+    if (p->prec == HS_F32)
+        k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, (const float*)Xadd, L, N, gpart);
+    else
+        k_gram<double><<<GRAM_CTAS, 256, 0, s>>>((const double*)X, (const double*)Xadd, L, N, gpart);
+    HS_CHECK_LAUNCH();
+    k_gram_reduce<<<P, 128, 0, s>>>(gpart, GRAM_CTAS, L, p->gram);
+    HS_CHECK_LAUNCH();
+    const size_t jsm = 2 * sizeof(double) * MAX_L_NUC * (MAX_L_NUC + 1);
+    k_jacobi<<<1, 1024, jsm, s>>>(p->gram, L, w_sv, thr, dual, p->eigf, sv_out, 40);
+    HS_CHECK_LAUNCH();
+    if (p->prec == HS_F32) return lowrank_apply_t<float>(p, X, Xadd, out, s);
+    return lowrank_apply_t<double>(p, X, Xadd, out, s);
+}
+
+hs_status prox_init() {
+    static bool done = false;
+    if (done) return HS_OK;
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * sizeof(double) * MAX_L_NUC * (MAX_L_NUC + 1))));
+    done = true;
+    return HS_OK;
+}
+
+int64_t gram_part_doubles(int L) { return (int64_t)(L * (L + 1) / 2) * GRAM_CTAS; }
+
+// ---------------------------------------------------------------- primal update
+template <typename R>
+__global__ void k_primal(int64_t n, const R* __restrict__ P, const R* __restrict__ At,
+                         const R* __restrict__ D, R k1, R k2, R k3, R tau, R* __restrict__ X,
+                         R* __restrict__ Xt, double* __restrict__ part) {
+    __shared__ double red[32];
+    double dd = 0.0, xx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        R g = k3 * D[i];
+        if (P) g = fma(k1, P[i], g);
+        if (At) g = fma(k2, At[i], g);
+        const R xo = X[i];
+        R xn = xo - tau * g;
+        xn = xn > (R)0 ? xn : (R)0;
+        X[i] = xn;
+        Xt[i] = (R)2 * xn - xo;
+        const double df = (double)xn - (double)xo;
+        dd += df * df;
+        xx += (double)xn * (double)xn;
+    }
+    dd = block_sum(dd, red);
+    xx = block_sum(xx, red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = dd;
+        part[2 * blockIdx.x + 1] = xx;
+    }
+}
+
+__global__ void k_beta(const double* __restrict__ part, int nb, double* __restrict__ beta) {
+    __shared__ double red[32];
+    double dd = 0.0, xx = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        dd += part[2 * b];
+        xx += part[2 * b + 1];
+    }
+    dd = block_sum(dd, red);
+    xx = block_sum(xx, red);
+    if (threadIdx.x == 0) *beta = (xx > 0.0) ? sqrt(dd / xx) : INFINITY;
+}
+
+hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const void* D,
+                        double k1, double k2, double k3, double tau, int use_p, int use_a,
+                        void* X, void* Xt, double* part, int nparts, cudaStream_t s) {
+    if (p->prec == HS_F32)
+        k_primal<float><<<nparts, 256, 0, s>>>(n, use_p ? (const float*)P : nullptr,
+                                               use_a ? (const float*)At : nullptr, (const float*)D,
+                                               (float)k1, (float)k2, (float)k3, (float)tau,
+                                               (float*)X, (float*)Xt, part);
+    else
+        k_primal<double><<<nparts, 256, 0, s>>>(n, use_p ? (const double*)P : nullptr,
+                                                use_a ? (const double*)At : nullptr,
+                                                (const double*)D, k1, k2, k3, tau, (double*)X,
+                                                (double*)Xt, part);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status beta_from_partials(const double* part, int nparts, double* beta, cudaStream_t s) {
+    k_beta<<<1, 256, 0, s>>>(part, nparts, beta);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------- channel norms (power iteration)
+template <typename R>
+__global__ void k_channel_norm(const R* __restrict__ X, int64_t N, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int l = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = (double)X[(int64_t)l * N + i];
+        s += v * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[l] = sqrt(s);
+}
+
+template <typename R>
+__global__ void k_channel_scale(R* __restrict__ X, int64_t N, const double* __restrict__ nrm) {
+    const int l = blockIdx.y;
+    const double nv = nrm[l];
+    const R f = (R)(nv > 0.0 ? 1.0 / nv : 0.0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)l * N + i] *= f;
+}
+
+hs_status channel_norms(Plan* p, const void* X, double* out_dev, cudaStream_t s) {
+    if (p->prec == HS_F32) k_channel_norm<float><<<p->g.L, 512, 0, s>>>((const float*)X, p->N(), out_dev);
+    else k_channel_norm<double><<<p->g.L, 512, 0, s>>>((const double*)X, p->N(), out_dev);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status scale_channels(Plan* p, void* X, const double* norms, cudaStream_t s) {
+    dim3 g(64, p->g.L);
+    if (p->prec == HS_F32) k_channel_scale<float><<<g, 256, 0, s>>>((float*)X, p->N(), norms);
+    else k_channel_scale<double><<<g, 256, 0, s>>>((double*)X, p->N(), norms);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+}  // namespace hs

@@ -1,0 +1,349 @@
+"""Thin ctypes binding of libhypersara.so (include/hypersara.h).
+
+Argument marshalling only: every operation runs in the library's CUDA
+kernels. Tensors are torch tensors on the CUDA device, contiguous, of the
+plan's precision (FP32 plan: float32 / complex64, FP64 plan: float64 /
+complex128). Calls are asynchronous on torch's current CUDA stream unless the
+C function documents a synchronisation. There is no CPU fallback: if the
+library is missing or fails to load, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhypersara.so")
+
+HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_NOMEM, HS_ERR_TIMEOUT, HS_ERR_STATE = 0, -1, -2, -3, -4, -5
+HS_F32, HS_F64 = 0, 1
+HS_PLAN_COMPENSATED = 1
+
+_lib = None
+
+
+class HSError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("L", C.c_int), ("Kx", C.c_int), ("Ky", C.c_int),
+                ("levels", C.c_int), ("prec", C.c_int), ("flags", C.c_int),
+                ("total_vis", C.c_int64), ("grid_tile_entries", C.c_int64),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("kb_terms", C.c_int),
+                ("kb_beta", C.c_double), ("kb_fit_max_err", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+class PDParams(C.Structure):
+    _fields_ = [("tau", C.c_double), ("kappa1", C.c_double), ("kappa2", C.c_double),
+                ("kappa3", C.c_double), ("mu", C.c_double), ("psi_norm2", C.c_double),
+                ("use_nuclear", C.c_int), ("use_l21", C.c_int),
+                ("w_nuc", C.c_void_p), ("w_l21", C.c_void_p)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "hs_version": ([], C.c_char_p),
+    "hs_last_error": ([], C.c_char_p),
+    "hs_plan_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64), _P, _P,
+                        _P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint, _P], C.c_int),
+    "hs_plan_destroy": ([_P], C.c_int),
+    "hs_plan_info": ([_P, C.POINTER(PlanInfo)], C.c_int),
+    "hs_phi_fwd": ([_P, _P, _P, _P], C.c_int),
+    "hs_phi_adj": ([_P, _P, _P, _P], C.c_int),
+    "hs_psi_fwd": ([_P, _P, _P, _P], C.c_int),
+    "hs_psi_adj": ([_P, _P, _P, _P], C.c_int),
+    "hs_prox_l21": ([_P, _P, _P, C.c_double, C.c_int, _P, _P], C.c_int),
+    "hs_prox_nuclear": ([_P, _P, _P, C.c_double, C.c_int, _P, _P, _P], C.c_int),
+    "hs_proj_l2ball": ([_P, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
+    "hs_norm_l21": ([_P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
+    "hs_op_norm2": ([_P, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double), _P], C.c_int),
+    "hs_pd_state_create": ([_P, _P, _P, C.POINTER(PDParams), C.POINTER(C.c_void_p), _P], C.c_int),
+    "hs_pd_state_destroy": ([_P], C.c_int),
+    "hs_pd_set_data": ([_P, _P, _P, _P], C.c_int),
+    "hs_pd_step": ([_P, _P], C.c_int),
+    "hs_pd_solve": ([_P, C.c_int, C.c_int, _P], C.c_int),
+    "hs_pd_get": ([_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
+    "hs_pd_iterations": ([_P, C.POINTER(C.c_int64)], C.c_int),
+    "hs_pd_graph_kernels": ([_P, C.POINTER(C.c_int)], C.c_int),
+    "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: Optional[str] = None):
+    """Load the library (once). Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                           f"g.build()'` (nvcc, sm_103a)")
+    lib = C.CDLL(p)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(fn: str, st: int):
+    if st != HS_OK:
+        msg = load().hs_last_error().decode(errors="replace")
+        raise HSError(fn, st, msg)
+
+
+def version() -> str:
+    return load().hs_version().decode()
+
+
+def daubechies_lowpass(p: int) -> np.ndarray:
+    out = (C.c_double * (2 * p))()
+    _check("hs_daubechies_lowpass", load().hs_daubechies_lowpass(p, out))
+    return np.array(out[:], dtype=np.float64)
+
+
+def kb_poly_fit_error(beta: float, terms: int, J: int = 8) -> float:
+    e = C.c_double()
+    _check("hs_kb_poly_fit", load().hs_kb_poly_fit(J, beta, terms, C.byref(e)))
+    return e.value
+
+
+# ---------------------------------------------------------------- torch glue
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Measurement plan (hs_plan_create). uv: CUDA tensor (M, 2) of the plan's real dtype."""
+
+    def __init__(self, nx: int, ny: int, offsets: Sequence[int], uv, weights=None, precond=None,
+                 oversample: int = 2, J: int = 8, kb_beta: float = 0.0, levels: int = 4,
+                 prec: str = "f32", compensated: bool = False):
+        torch = _torch()
+        lib = load()
+        self.nx, self.ny = int(nx), int(ny)
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.offsets = off
+        self.L = len(off) - 1
+        self.prec = prec
+        self.rdtype = torch.float32 if prec == "f32" else torch.float64
+        self.cdtype = torch.complex64 if prec == "f32" else torch.complex128
+        for name, t in (("uv", uv), ("weights", weights), ("precond", precond)):
+            if t is not None and t.dtype != self.rdtype:
+                raise ValueError(f"{name} must have dtype {self.rdtype}")
+        self._keep = (uv, weights, precond)
+        h = C.c_void_p()
+        st = lib.hs_plan_create(C.byref(h), self.nx, self.ny, self.L,
+                                off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
+                                _ptr(precond), oversample, J, float(kb_beta), levels,
+                                HS_F32 if prec == "f32" else HS_F64,
+                                HS_PLAN_COMPENSATED if compensated else 0, _stream())
+        _check("hs_plan_create", st)
+        self.h = h
+        self._keep = None
+        self.M = int(off[-1])
+
+    # sizes ----------------------------------------------------------------
+    @property
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check("hs_plan_info", load().hs_plan_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def cube(self, n_bases: int = 0):
+        torch = _torch()
+        shape = (self.L, self.ny, self.nx) if n_bases == 0 else (n_bases, self.L, self.ny, self.nx)
+        return torch.empty(shape, dtype=self.rdtype, device="cuda")
+
+    def vis(self):
+        torch = _torch()
+        return torch.empty(self.M, dtype=self.cdtype, device="cuda")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hs_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # operators --------------------------------------------------------------
+    def phi_fwd(self, X, Y=None):
+        Y = self.vis() if Y is None else Y
+        _check("hs_phi_fwd", load().hs_phi_fwd(self.h, _ptr(X), _ptr(Y), _stream()))
+        return Y
+
+    def phi_adj(self, Y, X=None):
+        X = self.cube() if X is None else X
+        _check("hs_phi_adj", load().hs_phi_adj(self.h, _ptr(Y), _ptr(X), _stream()))
+        return X
+
+    def psi_fwd(self, X, A=None):
+        A = self.cube(9) if A is None else A
+        _check("hs_psi_fwd", load().hs_psi_fwd(self.h, _ptr(X), _ptr(A), _stream()))
+        return A
+
+    def psi_adj(self, A, X=None):
+        X = self.cube() if X is None else X
+        _check("hs_psi_adj", load().hs_psi_adj(self.h, _ptr(A), _ptr(X), _stream()))
+        return X
+
+    def prox_l21(self, A, thr: float, w_rows=None, dual: bool = False, out=None):
+        out = self.cube(9) if out is None else out
+        _check("hs_prox_l21", load().hs_prox_l21(self.h, _ptr(A), _ptr(w_rows), float(thr), int(dual),
+                                                 _ptr(out), _stream()))
+        return out
+
+    def prox_nuclear(self, X, thr: float, w_sv=None, dual: bool = False, out=None):
+        """Returns (out, singular values as an FP64 CUDA tensor)."""
+        torch = _torch()
+        out = self.cube() if out is None else out
+        sv = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        _check("hs_prox_nuclear", load().hs_prox_nuclear(self.h, _ptr(X), _ptr(w_sv), float(thr),
+                                                         int(dual), _ptr(out), _ptr(sv), _stream()))
+        return out, sv
+
+    def proj_l2ball(self, Z, Yd, eps, dual: bool = False, out=None):
+        """eps: FP64 CUDA tensor (L,). Returns (out, rho) with rho = ||z_l - y_l||."""
+        torch = _torch()
+        out = self.vis() if out is None else out
+        rho = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        _check("hs_proj_l2ball", load().hs_proj_l2ball(self.h, _ptr(Z), _ptr(Yd), _ptr(eps), int(dual),
+                                                       _ptr(out), _ptr(rho), _stream()))
+        return out, rho
+
+    def norm_l21(self, A, w_rows=None) -> float:
+        r = C.c_double()
+        _check("hs_norm_l21", load().hs_norm_l21(self.h, _ptr(A), _ptr(w_rows), C.byref(r), _stream()))
+        return r.value
+
+    def op_norm2(self, iters: int = 500, tol: float = 1e-10, seed: int = 0) -> float:
+        r = C.c_double()
+        _check("hs_op_norm2", load().hs_op_norm2(self.h, int(iters), float(tol), int(seed), C.byref(r),
+                                                 _stream()))
+        return r.value
+
+
+class PDState:
+    """Algorithm 2 state (hs_pd_state_create). Y: CUDA complex tensor (caller order);
+    eps: FP64 CUDA tensor (L,)."""
+
+    def __init__(self, plan: Plan, Y, eps, *, tau: float = 0.33, kappa1: float = 1.0,
+                 kappa2: float = 1.0, kappa3: float = 1.0, mu: float = 0.0, psi_norm2: float = 1.0,
+                 use_nuclear: bool = True, use_l21: bool = True, w_nuc=None, w_l21=None):
+        self.plan = plan
+        self._refs = (w_nuc, w_l21)   # the state references these buffers
+        prm = PDParams(tau, kappa1, kappa2, kappa3, mu, psi_norm2, int(use_nuclear), int(use_l21),
+                       None if w_nuc is None else w_nuc.data_ptr(),
+                       None if w_l21 is None else w_l21.data_ptr())
+        h = C.c_void_p()
+        _check("hs_pd_state_create", load().hs_pd_state_create(plan.h, _ptr(Y), _ptr(eps), C.byref(prm),
+                                                               C.byref(h), _stream()))
+        self.h = h
+
+    def set_data(self, Y, eps):
+        _check("hs_pd_set_data", load().hs_pd_set_data(self.h, _ptr(Y), _ptr(eps), _stream()))
+
+    def step(self):
+        _check("hs_pd_step", load().hs_pd_step(self.h, _stream()))
+
+    def solve(self, iters: int, graph: bool = True):
+        _check("hs_pd_solve", load().hs_pd_solve(self.h, int(iters), int(graph), _stream()))
+
+    def get(self, X=None):
+        """Returns (X copy, beta, rho per channel as numpy)."""
+        X = self.plan.cube() if X is None else X
+        beta = C.c_double()
+        rho = (C.c_double * self.plan.L)()
+        _check("hs_pd_get", load().hs_pd_get(self.h, _ptr(X), C.byref(beta), rho, _stream()))
+        return X, beta.value, np.array(rho[:])
+
+    @property
+    def graph_kernels(self) -> int:
+        n = C.c_int()
+        _check("hs_pd_graph_kernels", load().hs_pd_graph_kernels(self.h, C.byref(n)))
+        return n.value
+
+    @property
+    def iterations(self) -> int:
+        n = C.c_int64()
+        _check("hs_pd_iterations", load().hs_pd_iterations(self.h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hs_pd_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# Functional names matching the C ABI ----------------------------------------
+def phi_fwd(plan: Plan, X, Y=None):
+    return plan.phi_fwd(X, Y)
+
+
+def phi_adj(plan: Plan, Y, X=None):
+    return plan.phi_adj(Y, X)
+
+
+def psi_fwd(plan: Plan, X, A=None):
+    return plan.psi_fwd(X, A)
+
+
+def psi_adj(plan: Plan, A, X=None):
+    return plan.psi_adj(A, X)
+
+
+def prox_l21(plan: Plan, A, thr, w_rows=None, dual=False, out=None):
+    return plan.prox_l21(A, thr, w_rows, dual, out)
+
+
+def prox_nuclear(plan: Plan, X, thr, w_sv=None, dual=False, out=None):
+    return plan.prox_nuclear(X, thr, w_sv, dual, out)
+
+
+def proj_l2ball(plan: Plan, Z, Yd, eps, dual=False, out=None):
+    return plan.proj_l2ball(Z, Yd, eps, dual, out)
+
+
+def pd_step(state: PDState):
+    state.step()
+
+
+def pd_solve(state: PDState, iters: int, graph: bool = True):
+    state.solve(iters, graph)

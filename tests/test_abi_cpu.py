@@ -1,0 +1,78 @@
+"""CPU-side checks of the C ABI: the library loads without a GPU, exports every
+function declared in include/hypersara.h, and its host-only helpers agree with
+the oracle's independently derived tables (Daubechies filters by a different
+root finder; the Kaiser-Bessel fit against the kernel definition)."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hypersara.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"HS_API\s+(?:hs_status|const char\*)\s+(hs_\w+)\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1806_04596_gb300 import hypersara as hs
+    return hs
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["hs_phi_fwd", "hs_phi_adj", "hs_psi_fwd", "hs_psi_adj", "hs_prox_l21",
+                     "hs_prox_nuclear", "hs_proj_l2ball", "hs_pd_step", "hs_pd_solve"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = lib.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert set(_declared()) == set(lib.EXPORTED)
+    assert "sm_103a" in lib.version()
+
+
+def test_library_is_built_for_sm103a_only():
+    from paper_1806_04596_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("p", range(1, 9))
+def test_library_daubechies_filters_match_oracle(lib, p):
+    from oracle import wavelets
+    np.testing.assert_allclose(lib.daubechies_lowpass(p), wavelets.daubechies_lowpass(p),
+                               rtol=0, atol=5e-15)
+
+
+def test_library_kb_fit_accuracy(lib):
+    beta = np.pi * np.sqrt(35.2)
+    # coefficients used by the FP32 (9) and FP64 (14) kernels
+    assert lib.kb_poly_fit_error(beta, 9) < 1e-8
+    assert lib.kb_poly_fit_error(beta, 14) < 2e-14
+
+
+def test_host_argument_errors_without_gpu(lib):
+    """Argument checks happen on the host before any device call."""
+    L = lib.load()
+    import ctypes as C
+    h = C.c_void_p()
+    off = np.array([0, 10], dtype=np.int64)
+    st = L.hs_plan_create(C.byref(h), 12, 16, 1, off.ctypes.data_as(C.POINTER(C.c_int64)), None, None,
+                          None, 2, 8, 0.0, 2, 0, 0, None)
+    assert st == lib.HS_ERR_ARG
+    assert b"powers of two" in L.hs_last_error()
+    st = L.hs_plan_create(C.byref(h), 16, 16, 1, off.ctypes.data_as(C.POINTER(C.c_int64)), None, None,
+                          None, 3, 8, 0.0, 2, 0, 0, None)
+    assert st == lib.HS_ERR_ARG
+    assert L.hs_phi_fwd(None, None, None, None) == lib.HS_ERR_ARG
+    assert L.hs_pd_step(None, None) == lib.HS_ERR_ARG
+    assert L.hs_plan_destroy(None) == lib.HS_OK
