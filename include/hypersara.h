@@ -66,7 +66,10 @@ typedef enum {
 typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
 
 /* plan flags */
-#define HS_PLAN_COMPENSATED 1u   /* FP32 gridding with compensated (Kahan) summation */
+/* Gridding with per-warp private tiles summed in a fixed order (bitwise
+ * reproducible), Kahan-compensated in FP32 plans. Without it gridding uses
+ * shared-memory atomic additions: faster, equal to rounding, order not fixed. */
+#define HS_PLAN_COMPENSATED 1u
 
 typedef struct hs_plan* hs_plan_t;
 typedef struct hs_pd_state* hs_pd_state_t;
@@ -79,7 +82,7 @@ HS_API const char* hs_last_error(void);
 
 /*
  * hs_plan_create - measurement setup for one wideband problem (Sec. 2.1).
- *   nx, ny        image size; powers of two, >= 16, divisible by 2^wavelet_levels.
+ *   nx, ny        image size; powers of two in [16, 2048], divisible by 2^wavelet_levels.
  *   L             number of channels, 1..1024 (the nuclear-norm prox needs L <= 64).
  *   vis_offsets   HOST array of L+1 int64: visibilities of channel l are
  *                 [vis_offsets[l], vis_offsets[l+1]); vis_offsets[0] = 0,
@@ -174,6 +177,11 @@ HS_API hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, 
  * w_sv: DEVICE L doubles (weight of the j-th largest singular value) or NULL
  * for 1. sv_out: DEVICE L doubles receiving the singular values of X in
  * descending order, or NULL. Requires L <= 64. out may equal X.
+ * FP64 plans diagonalise the Gram matrix with an FP64 Jacobi method. FP32 plans
+ * use an FP32 Jacobi method for the whole spectrum and refine in FP64 the
+ * eigenpairs with sigma_j > thr w_j (the only ones whose factor differs from 1
+ * in the dual form or from 0 in the prox form); singular values below the
+ * threshold are then resolved to ~1e-7 sigma_max^2 / sigma_j.
  */
 HS_API hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, double thr,
                           int dual, void* out, double* sv_out, void* stream);
@@ -264,6 +272,15 @@ HS_API hs_status hs_pd_get(hs_pd_state_t state, void* X, double* beta_host, doub
 /* Number of kernel nodes in the state's captured iteration graph (0 before the
  * first hs_pd_solve with graph = 1): the kernel launches of one iteration. */
 HS_API hs_status hs_pd_graph_kernels(hs_pd_state_t state, int* out);
+
+/*
+ * hs_pd_nuclear_info - diagnostics of the last nuclear-norm step (Algorithm 2
+ * step 5) of a state: sv_host (HOST L doubles, may be NULL) receives the
+ * singular values of P + X~, *active_host (may be NULL) the number of them above
+ * the threshold. Synchronises the stream.
+ */
+HS_API hs_status hs_pd_nuclear_info(hs_pd_state_t state, double* sv_host, int* active_host,
+                                    void* stream);
 
 /* Number of iterations performed by a state. */
 HS_API hs_status hs_pd_iterations(hs_pd_state_t state, int64_t* out);

@@ -42,11 +42,14 @@ struct hs_pd_state {
     double* beta = nullptr; // 1
     double* ppart = nullptr;   // primal partial sums
     double* dpart = nullptr;   // de-gridding partial sums
+    float* warm = nullptr;     // L x L eigenvectors of the previous nuclear step (FP32 plans)
+    double* sv = nullptr;      // L singular values of the last nuclear step
+    int* nact = nullptr;       // active count of the last nuclear step
     int nprim = 0;
     int nbx = 0;
     int64_t iters = 0;
-    cudaStream_t side = nullptr, cap = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr, cap = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     std::vector<void*> allocs;
@@ -200,7 +203,8 @@ hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, dou
     if (dual != 0 && dual != 1) return fail(HS_ERR_ARG, "hs_prox_nuclear: dual must be 0 or 1");
     if (plan->p->g.L > MAX_L_NUC)
         return fail(HS_ERR_ARG, "hs_prox_nuclear: L = %d exceeds %d", plan->p->g.L, MAX_L_NUC);
-    return nuclear_apply(plan->p, X, nullptr, w_sv, thr, dual, out, sv_out, S(stream));
+    return nuclear_apply(plan->p, X, nullptr, w_sv, thr, dual, out, sv_out, nullptr, nullptr,
+                         S(stream));
 }
 
 hs_status hs_proj_l2ball(hs_plan_t plan, const void* Z, const void* Yd, const double* eps, int dual,
@@ -316,7 +320,9 @@ static void st_free(hs_pd_state* st) {
     if (st->graph) cudaGraphDestroy(st->graph);
     if (st->ev_fork) cudaEventDestroy(st->ev_fork);
     if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->ev_join2) cudaEventDestroy(st->ev_join2);
     if (st->side) cudaStreamDestroy(st->side);
+    if (st->side2) cudaStreamDestroy(st->side2);
     if (st->cap) cudaStreamDestroy(st->cap);
     for (void* q : st->allocs) cudaFree(q);
     st->allocs.clear();
@@ -383,6 +389,9 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     ALLOC(st->ppart, 2 * st->nprim * sizeof(double));
     st->nbx = std::max(1, degrid_blocks_x(p));
     ALLOC(st->dpart, (size_t)L * st->nbx * sizeof(double));
+    ALLOC(st->warm, (size_t)MAX_L_NUC * MAX_L_NUC * sizeof(float));
+    ALLOC(st->sv, (size_t)std::max(L, 1) * sizeof(double));
+    ALLOC(st->nact, sizeof(int));
 #undef ALLOC
     auto cu = [&](cudaError_t ce, const char* what) -> hs_status {
         if (ce == cudaSuccess) return HS_OK;
@@ -397,7 +406,16 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     HS_TRY(cu(cudaMemsetAsync(st->v, 0, std::max<int64_t>(M, 1) * cs, s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->beta, 0, sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->rho, 0, L * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->sv, 0, L * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->nact, 0, sizeof(int), s), "memset"));
     HS_TRY(cu(cudaMemcpyAsync(st->eps, eps, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "eps"));
+    if (L <= MAX_L_NUC) {   // warm start of the eigensolver: identity
+        std::vector<float> eye((size_t)L * L, 0.f);
+        for (int i = 0; i < L; ++i) eye[(size_t)i * L + i] = 1.f;
+        HS_TRY(cu(cudaMemcpyAsync(st->warm, eye.data(), eye.size() * sizeof(float),
+                                  cudaMemcpyHostToDevice, s), "warm"));
+        HS_TRY(cu(cudaStreamSynchronize(s), "sync"));
+    }
     if (M > 0) {
         const unsigned g = (unsigned)std::min<int64_t>((M + 255) / 256, 8192);
         if (p->prec == HS_F32) k_gather_c2<<<g, 256, 0, s>>>((const float2*)Y, p->perm, (float2*)st->y, M);
@@ -405,6 +423,8 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
         HS_TRY(cu(cudaGetLastError(), "gather"));
     }
     HS_TRY(cu(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking), "stream"));
+    HS_TRY(cu(cudaStreamCreateWithFlags(&st->side2, cudaStreamNonBlocking), "stream"));
+    HS_TRY(cu(cudaEventCreateWithFlags(&st->ev_join2, cudaEventDisableTiming), "event"));
     HS_TRY(cu(cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking), "stream"));
     HS_TRY(cu(cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming), "event"));
     HS_TRY(cu(cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming), "event"));
@@ -438,25 +458,30 @@ hs_status hs_pd_state_destroy(hs_pd_state_t st) {
     return HS_OK;
 }
 
-// One iteration of Algorithm 2 on stream s. The prior branch (steps 5, 7, 8)
-// runs on the state's side stream, forked and joined with events, so it
-// overlaps the data-fidelity branch (steps 4, 10-12 and Phi^dagger of step 20).
+// One iteration of Algorithm 2 on stream s. The two prior branches (step 5;
+// steps 7-8) run on the state's two side streams, forked and joined with
+// events, so they overlap each other and the data-fidelity branch (steps 4,
+// 10-12 and Phi^dagger of step 20). They use disjoint scratch: the nuclear
+// branch the Gram buffers, the sparsity branch the wavelet buffers.
 static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
     Plan* p = st->p;
     const hs_pd_params& q = st->prm;
     const int64_t n = (int64_t)p->g.L * p->N();
     HS_CHECK_CUDA(cudaEventRecord(st->ev_fork, s));
     HS_CHECK_CUDA(cudaStreamWaitEvent(st->side, st->ev_fork, 0));
+    HS_CHECK_CUDA(cudaStreamWaitEvent(st->side2, st->ev_fork, 0));
     // ---- priors (side stream)
     if (q.use_nuclear)   // step 5: P = (I - S*_w)(P + X~), threshold w / kappa1
-        HS_TRY(nuclear_apply(p, st->P, st->Xt, q.w_nuc, 1.0 / q.kappa1, 1, st->P, nullptr, st->side));
-    if (q.use_l21) {     // steps 7-8
-        HS_TRY(dwt_analysis(p, st->Xt, st->W, st->side));
-        // A_d = (I - S^{l21}_{w mu ||Psi||^2})(A_d + Psi_d^dagger X~)
-        HS_TRY(l21_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side));
-        HS_TRY(dwt_synthesis(p, st->A, st->At, st->side));
-    }
+        HS_TRY(nuclear_apply(p, st->P, st->Xt, q.w_nuc, 1.0 / q.kappa1, 1, st->P, st->sv, st->warm,
+                             st->nact, st->side));
     HS_CHECK_CUDA(cudaEventRecord(st->ev_join, st->side));
+    if (q.use_l21) {     // steps 7-8
+        HS_TRY(dwt_analysis(p, st->Xt, st->W, st->side2));
+        // A_d = (I - S^{l21}_{w mu ||Psi||^2})(A_d + Psi_d^dagger X~)
+        HS_TRY(l21_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side2));
+        HS_TRY(dwt_synthesis(p, st->A, st->At, st->side2));
+    }
+    HS_CHECK_CUDA(cudaEventRecord(st->ev_join2, st->side2));
     // ---- data fidelity (main stream)
     if (p->M_total > 0) {
         HS_TRY(fft_forward(p, st->Xt, s));                        // step 4
@@ -479,6 +504,7 @@ static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
         HS_CHECK_CUDA(cudaMemsetAsync(st->D, 0, n * p->rsize(), s));
     }
     HS_CHECK_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
+    HS_CHECK_CUDA(cudaStreamWaitEvent(s, st->ev_join2, 0));
     // ---- steps 20-23
     HS_TRY(primal_update(p, n, st->P, st->At, st->D, q.kappa1, q.kappa2, q.kappa3, q.tau,
                          q.use_nuclear, q.use_l21, st->X, st->Xt, st->ppart, st->nprim, s));
@@ -558,6 +584,19 @@ hs_status hs_pd_graph_kernels(hs_pd_state_t st, int* out) {
         if (t == cudaGraphNodeTypeKernel) ++k;
     }
     *out = k;
+    return HS_OK;
+}
+
+hs_status hs_pd_nuclear_info(hs_pd_state_t st, double* sv_host, int* active_host, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_nuclear_info: state is null");
+    cudaStream_t s = S(stream);
+    if (sv_host)
+        HS_CHECK_CUDA(cudaMemcpyAsync(sv_host, st->sv, sizeof(double) * st->p->g.L,
+                                      cudaMemcpyDeviceToHost, s));
+    if (active_host)
+        HS_CHECK_CUDA(cudaMemcpyAsync(active_host, st->nact, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
 }
 

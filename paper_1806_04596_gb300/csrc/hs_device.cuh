@@ -115,4 +115,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return v;
 }
 
+// Block-wide sum returned to every thread (uses red[0..32]).
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) red[32] = v;
+    __syncthreads();
+    v = red[32];
+    __syncthreads();
+    return v;
+}
+
 }  // namespace hs

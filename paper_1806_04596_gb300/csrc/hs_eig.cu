@@ -1,0 +1,521 @@
+// Eigendecomposition of the L x L Gram matrix S = Z^T Z for the nuclear-norm
+// prox (Eq. "prox-L*") of FP32 plans, in one CTA.
+//
+// The prox needs V diag(f) V^T with f_j = min(1, c_j / sigma_j) (dual form,
+// Algorithm 2 step 5) or max(0, 1 - c_j / sigma_j) (prox form), sigma_j =
+// sqrt(lambda_j). Only eigenpairs with sigma_j > c_j make f_j differ from its
+// limit (1 for the dual, 0 for the prox), so only those "active" pairs must be
+// accurate; on GB300 FP64 is ~1/64 of the FP32 rate, so the work is split:
+//
+//  1. FP32 cyclic Jacobi (round-robin parallel ordering) on S, warm-started
+//     from the previous call's eigenvectors V0 (A = V0^T S V0), gives every
+//     eigenpair to FP32 accuracy.
+//  2. The active eigenvectors are refined in FP64 against the rest of the
+//     basis with two first-order correction steps of an approximate
+//     eigendecomposition (Ogita & Aishima 2018): with b_j the basis, T = B^T S X,
+//     R = I - B^T X, lambda_c = T_cc / (1 - R_cc), the correction of x_c along
+//     b_j is (T_jc + lambda_c R_jc) / (lambda_c - lambda_j) across the active /
+//     inactive boundary and R_jc / 2 (orthogonalisation only) inside the active
+//     set or for near-equal eigenvalues (those straddle the threshold, where f
+//     is continuous, so their mixing does not change the result).
+//  3. Modified Gram-Schmidt, then an FP64 Rayleigh-Ritz step on the active
+//     subspace (FP64 Jacobi on the r x r matrix X^T S X) resolves the
+//     eigenpairs inside it.
+//  4. Mf = I - sum_active (1 - f) x x^T (dual) or sum_active f x x^T (prox).
+#include <cmath>
+
+#include "hs_device.cuh"
+#include "hs_internal.h"
+
+namespace hs {
+
+constexpr int EIG_T = 1024;
+constexpr int LD32 = MAX_L_NUC + 1;
+
+// Block-wide sum of doubles, returned to every thread (red: 33 doubles).
+__device__ __forceinline__ double eig_bsum(double v, double* red) { return block_sum_all(v, red); }
+
+// Round-robin (circle method) schedule for n indices, n even: in round r the
+// index n-1 meets r and (r + i) meets (r - i) (mod n-1) for i = 1 .. n/2-1.
+// partner[r * n + i] is the index paired with i in round r.
+__device__ void rr_schedule(int n, signed char* partner) {
+    for (int k = threadIdx.x; k < (n - 1) * n; k += blockDim.x) {
+        const int r = k / n, i = k - r * n;
+        int pi;
+        if (i == n - 1) pi = r;
+        else if (i == r) pi = n - 1;
+        else pi = ((2 * r - i) % (n - 1) + (n - 1)) % (n - 1);
+        partner[k] = (signed char)pi;
+    }
+}
+
+// Cyclic Jacobi, round-robin parallel ordering, on the symmetric N x N matrix
+// in A (leading dimension LDJ), accumulating V <- V J; B and W are scratch of
+// the same shape. Each round, every index i computes the rotation of its pair
+// (p, q) from a_pp, a_qq, a_pq (symmetric Schur decomposition, Golub & Van Loan
+// Alg. 8.4.1), then every entry is updated at once from four old entries:
+//   A'_ij = c_i c_j A_ij + c_i t_j A_i,pj + t_i c_j A_pi,j + t_i t_j A_pi,pj,
+//   V'_kj = c_j V_kj + t_j V_k,pj,
+// with t_p = -s, t_q = +s (J_pp = J_qq = c, J_pq = s, J_qp = -s). A rotation is
+// applied only when |a_pq| exceeds skip sqrt(|a_pp a_qq|) and floor_rel ||A||_F;
+// sweeps stop when the off-diagonal Frobenius norm is at most off_rel ||A||_F,
+// when a sweep applies no rotation, or after max_sweeps. The result is left
+// in A and V.
+template <typename T, int N>
+__device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partner, double skip,
+                                double floor_rel, double off_rel, int max_sweeps, T* cvec, T* tvec,
+                                double* red, int* flag) {
+    constexpr int LDJ = MAX_L_NUC + 1;
+    constexpr int LG = (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    T *a = A, *b = B, *v = V, *w = W;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        double nrm = 0.0, off = 0.0;
+        for (int k = tid; k < N * N; k += nt) {
+            const int i = k >> LG, j = k & (N - 1);
+            const double x = (double)a[i * LDJ + j];
+            nrm += x * x;
+            if (i != j) off += x * x;
+        }
+        nrm = eig_bsum(nrm, red);
+        off = eig_bsum(off, red);
+        if (!(off > off_rel * off_rel * nrm)) break;
+        const double flo = floor_rel * sqrt(nrm);
+        if (tid == 0) *flag = 0;
+        __syncthreads();
+        for (int r = 0; r < N - 1; ++r) {
+            const signed char* pr = partner + r * N;
+            if (tid < N) {
+                const int i = tid, pi = pr[i];
+                const int p = i < pi ? i : pi, q = i < pi ? pi : i;
+                const T apq = a[p * LDJ + q], app = a[p * LDJ + p], aqq = a[q * LDJ + q];
+                T c = 1, s = 0;
+                const double ab = fabs((double)apq);
+                if (ab > flo && ab > 1e-300 && ab > skip * sqrt(fabs((double)app * (double)aqq))) {
+                    const T tau = (aqq - app) / (T(2) * apq);
+                    const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+                    c = T(1) / sqrt(T(1) + t * t);
+                    s = t * c;
+                    *flag = 1;
+                }
+                cvec[i] = c;
+                tvec[i] = (i == p) ? -s : s;
+            }
+            __syncthreads();
+            for (int k = tid; k < 2 * N * N; k += nt) {
+                const int kk = k & (N * N - 1);
+                const int i = kk >> LG, j = kk & (N - 1);
+                const int pj = pr[j];
+                const T cj = cvec[j], tj = tvec[j];
+                if (k < N * N) {
+                    const int pi = pr[i];
+                    const T ci = cvec[i], ti = tvec[i];
+                    T x = ci * cj * a[i * LDJ + j];
+                    if (tj != T(0)) x = fma(ci * tj, a[i * LDJ + pj], x);
+                    if (ti != T(0)) {
+                        x = fma(ti * cj, a[pi * LDJ + j], x);
+                        if (tj != T(0)) x = fma(ti * tj, a[pi * LDJ + pj], x);
+                    }
+                    if (j == pi && ti != T(0)) x = T(0);   // the rotated pair is decoupled
+                    b[i * LDJ + j] = x;
+                } else {
+                    T x = cj * v[i * LDJ + j];
+                    if (tj != T(0)) x = fma(tj, v[i * LDJ + pj], x);
+                    w[i * LDJ + j] = x;
+                }
+            }
+            __syncthreads();
+            T* t1 = a;
+            a = b;
+            b = t1;
+            t1 = v;
+            v = w;
+            w = t1;
+        }
+        const int any = *flag;
+        __syncthreads();
+        if (!any) break;
+    }
+    if (a != A) {   // leave the result in A / V
+        for (int k = tid; k < N * N; k += nt) {
+            const int i = k >> LG, j = k & (N - 1);
+            A[i * LDJ + j] = a[i * LDJ + j];
+            V[i * LDJ + j] = v[i * LDJ + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Dispatch on the padded size n (power of two, 2..64).
+template <typename T>
+__device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, signed char* partner, double skip,
+                         double floor_rel, double off_rel, int max_sweeps, T* cvec, T* tvec,
+                         double* red, int* flag) {
+    rr_schedule(n, partner);
+    __syncthreads();
+#define HS_JAC(NN)                                                                                   \
+    jacobi_pairwise<T, NN>(A, B, V, W, partner, skip, floor_rel, off_rel, max_sweeps, cvec, tvec, red, \
+                           flag)
+    switch (n) {
+        case 2: HS_JAC(2); break;
+        case 4: HS_JAC(4); break;
+        case 8: HS_JAC(8); break;
+        case 16: HS_JAC(16); break;
+        case 32: HS_JAC(32); break;
+        default: HS_JAC(64); break;
+    }
+#undef HS_JAC
+}
+
+// One CTA of EIG_T threads; dynamic shared memory layout below.
+__global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ Sg, int L,
+                                                    const double* __restrict__ w_sv, double thr,
+                                                    int dual, double* __restrict__ Mf,
+                                                    double* __restrict__ sv_out,
+                                                    float* __restrict__ warm, int* __restrict__ r_out) {
+    extern __shared__ __align__(16) unsigned char eig_smem[];
+    constexpr int SL = MAX_L_NUC * LD32;                 // one 64 x 65 slot
+    float* V32 = (float*)eig_smem;                       // slot 0
+    float* W32 = V32 + SL;                               // slot 1 (Jacobi scratch)
+    float* A32 = W32 + SL;                               // slot 2
+    float* B32 = A32 + SL;                               // slot 3 (Jacobi scratch, warm-start temp)
+    float* T32 = B32;
+    double* Sd = (double*)(B32 + SL);                    // 64 x 65 doubles each from here
+    double* X = Sd + SL;                                 // active vectors (columns)
+    double* Y = X + SL;
+    double* Rb = Y + SL;
+    // FP64 views over the float slots once those are dead: slots 2-3 and slots 0-1
+    double* Tb = (double*)A32;
+    double* Ub = (double*)V32;
+    __shared__ double red[33];
+    __shared__ float cv32[MAX_L_NUC], tv32[MAX_L_NUC];
+    __shared__ double cv64[MAX_L_NUC], tv64[MAX_L_NUC];
+    __shared__ signed char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ int flag;
+    __shared__ double lam32[MAX_L_NUC], lamr[MAX_L_NUC], fv[MAX_L_NUC];
+    __shared__ int order[MAX_L_NUC], ordr[MAX_L_NUC];
+    __shared__ int r_act;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int n = 2;
+    while (n < L) n <<= 1;
+    // ---- load S (FP64) and its FP32 copy
+    for (int k = tid; k < n * n; k += nt) {
+        const int i = k / n, j = k - i * n;
+        const double v = (i < L && j < L) ? Sg[i * L + j] : 0.0;
+        Sd[i * MAX_L_NUC + j] = v;
+        A32[i * LD32 + j] = (float)v;
+        V32[i * LD32 + j] = (warm && i < L && j < L) ? warm[i * L + j] : (i == j ? 1.f : 0.f);
+    }
+    __syncthreads();
+    if (warm) {   // A = V0^T S V0 (FP32), then symmetrise
+        for (int k = tid; k < n * n; k += nt) {
+            const int i = k / n, j = k - i * n;
+            float acc = 0.f;
+            for (int m = 0; m < n; ++m) acc = fmaf(A32[i * LD32 + m], V32[m * LD32 + j], acc);
+            T32[i * LD32 + j] = acc;
+        }
+        __syncthreads();
+        for (int k = tid; k < n * n; k += nt) {
+            const int i = k / n, j = k - i * n;
+            float acc = 0.f;
+            for (int m = 0; m < n; ++m) acc = fmaf(V32[m * LD32 + i], T32[m * LD32 + j], acc);
+            A32[i * LD32 + j] = acc;
+        }
+        __syncthreads();
+        for (int k = tid; k < n * n; k += nt) {
+            const int i = k / n, j = k - i * n;
+            if (i < j) {
+                const float a = 0.5f * (A32[i * LD32 + j] + A32[j * LD32 + i]);
+                A32[i * LD32 + j] = a;
+                A32[j * LD32 + i] = a;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- 1. FP32 Jacobi on every eigenpair
+    // warm-started calls run at most two FP32 sweeps: the active pairs are made
+    // exact in FP64 below, and the basis keeps improving from call to call
+    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 2 : 15, cv32, tv32, red, &flag);
+    // ---- eigenvalues, descending order (rank by counting), warm start for the next call
+    if (tid < L) lam32[tid] = (double)A32[tid * LD32 + tid];
+    __syncthreads();
+    if (tid < L) {
+        int rk = 0;
+        const double li = lam32[tid];
+        for (int j = 0; j < L; ++j) {
+            const double lj = lam32[j];
+            rk += (lj > li) || (lj == li && j < tid);
+        }
+        order[rk] = tid;
+    }
+    if (warm)
+        for (int k = tid; k < L * L; k += nt) warm[k] = V32[(k / L) * LD32 + (k % L)];
+    __syncthreads();
+    if (tid == 0) {
+        int r = 0;
+        for (int j = 0; j < L; ++j) {
+            const double sig = sqrt(fmax(lam32[order[j]], 0.0));
+            const double c = thr * (w_sv ? w_sv[j] : 1.0);
+            if (sig > c * (1.0 - 1e-3)) r = j + 1;
+        }
+        r_act = r;
+        if (r_out) *r_out = r;
+    }
+    __syncthreads();
+    const int r = r_act;
+    if (r > 0) {
+        // active vectors in FP64
+        for (int k = tid; k < L * r; k += nt) {
+            const int i = k / r, c = k - i * r;
+            X[i * MAX_L_NUC + c] = (double)V32[i * LD32 + order[c]];
+        }
+        __syncthreads();
+        // ---- 2. two FP64 correction steps of the active vectors against the whole basis
+        for (int step = 0; step < 2; ++step) {
+            // Y = S X
+            for (int k = tid; k < L * r; k += nt) {
+                const int i = k / r, c = k - i * r;
+                double acc = 0.0;
+                for (int m = 0; m < L; ++m) acc = fma(Sd[i * MAX_L_NUC + m], X[m * MAX_L_NUC + c], acc);
+                Y[i * MAX_L_NUC + c] = acc;
+            }
+            __syncthreads();
+            // T_jc = b_j . Y_c, R_jc = delta_jc - b_j . X_c   (b_j = X_j for j < r, else V32 column)
+            for (int k = tid; k < L * r; k += nt) {
+                const int j = k / r, c = k - j * r;
+                double t = 0.0, q = 0.0;
+                if (j < r) {
+                    for (int m = 0; m < L; ++m) {
+                        const double b = X[m * MAX_L_NUC + j];
+                        t = fma(b, Y[m * MAX_L_NUC + c], t);
+                        q = fma(b, X[m * MAX_L_NUC + c], q);
+                    }
+                } else {
+                    const int col = order[j];
+                    for (int m = 0; m < L; ++m) {
+                        const double b = (double)V32[m * LD32 + col];
+                        t = fma(b, Y[m * MAX_L_NUC + c], t);
+                        q = fma(b, X[m * MAX_L_NUC + c], q);
+                    }
+                }
+                Tb[j * MAX_L_NUC + c] = t;
+                Rb[j * MAX_L_NUC + c] = (j == c ? 1.0 : 0.0) - q;
+            }
+            __syncthreads();
+            if (tid < r) lamr[tid] = Tb[tid * MAX_L_NUC + tid] / (1.0 - Rb[tid * MAX_L_NUC + tid]);
+            __syncthreads();
+            const double delta = 1e-5 * fmax(fabs(lamr[0]), 1e-300);
+            // E_jc into Tb (overwrites T in place: each entry read once by its own thread)
+            for (int k = tid; k < L * r; k += nt) {
+                const int j = k / r, c = k - j * r;
+                const double t = Tb[j * MAX_L_NUC + c], q = Rb[j * MAX_L_NUC + c];
+                double e;
+                if (j < r) {
+                    e = 0.5 * q;
+                } else {
+                    const double gap = lamr[c] - lam32[order[j]];
+                    e = (fabs(gap) > delta) ? (t + lamr[c] * q) / gap : 0.5 * q;
+                }
+                Tb[j * MAX_L_NUC + c] = e;
+            }
+            __syncthreads();
+            // X_new = X + B E  (into Y)
+            for (int k = tid; k < L * r; k += nt) {
+                const int i = k / r, c = k - i * r;
+                double acc = X[i * MAX_L_NUC + c];
+                for (int j = 0; j < r; ++j) acc = fma(X[i * MAX_L_NUC + j], Tb[j * MAX_L_NUC + c], acc);
+                for (int j = r; j < L; ++j)
+                    acc = fma((double)V32[i * LD32 + order[j]], Tb[j * MAX_L_NUC + c], acc);
+                Y[i * MAX_L_NUC + c] = acc;
+            }
+            __syncthreads();
+            for (int k = tid; k < L * r; k += nt) {
+                const int i = k / r, c = k - i * r;
+                X[i * MAX_L_NUC + c] = Y[i * MAX_L_NUC + c];
+            }
+            __syncthreads();
+        }
+        // ---- 3. modified Gram-Schmidt on the active vectors
+        for (int c = 0; c < r; ++c) {
+            for (int j = 0; j < c; ++j) {
+                double d = 0.0;
+                for (int m = tid; m < L; m += nt) d += X[m * MAX_L_NUC + j] * X[m * MAX_L_NUC + c];
+                d = eig_bsum(d, red);
+                if (tid == 0) red[31] = d;
+                __syncthreads();
+                d = red[31];
+                for (int m = tid; m < L; m += nt) X[m * MAX_L_NUC + c] -= d * X[m * MAX_L_NUC + j];
+                __syncthreads();
+            }
+            double nn = 0.0;
+            for (int m = tid; m < L; m += nt) nn += X[m * MAX_L_NUC + c] * X[m * MAX_L_NUC + c];
+            nn = eig_bsum(nn, red);
+            if (tid == 0) red[31] = nn;
+            __syncthreads();
+            const double inv = 1.0 / sqrt(red[31]);
+            for (int m = tid; m < L; m += nt) X[m * MAX_L_NUC + c] *= inv;
+            __syncthreads();
+        }
+        //      Rayleigh-Ritz: Tr = X^T S X (r x r), FP64 Jacobi, X <- X W
+        int nr = 2;
+        while (nr < r) nr <<= 1;
+        for (int k = tid; k < L * r; k += nt) {
+            const int i = k / r, c = k - i * r;
+            double acc = 0.0;
+            for (int m = 0; m < L; ++m) acc = fma(Sd[i * MAX_L_NUC + m], X[m * MAX_L_NUC + c], acc);
+            Y[i * MAX_L_NUC + c] = acc;
+        }
+        __syncthreads();
+        for (int k = tid; k < nr * nr; k += nt) {
+            const int a = k / nr, b = k - a * nr;
+            double acc = 0.0;
+            if (a < r && b < r)
+                for (int m = 0; m < L; ++m) acc = fma(X[m * MAX_L_NUC + a], Y[m * MAX_L_NUC + b], acc);
+            Tb[a * LD32 + b] = acc;
+            Rb[a * LD32 + b] = (a == b) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        for (int k = tid; k < nr * nr; k += nt) {   // symmetrise
+            const int a = k / nr, b = k - a * nr;
+            if (a < b) {
+                const double v = 0.5 * (Tb[a * LD32 + b] + Tb[b * LD32 + a]);
+                Tb[a * LD32 + b] = v;
+                Tb[b * LD32 + a] = v;
+            }
+        }
+        __syncthreads();
+        jacobi_n<double>(nr, Tb, Ub, Rb, Sd, partner, 1e-16, 1e-17, 1e-15, 40, cv64, tv64, red, &flag);
+        if (tid < r) lamr[tid] = Tb[tid * LD32 + tid];
+        __syncthreads();
+        if (tid < r) {
+            int rk = 0;
+            const double li = lamr[tid];
+            for (int j = 0; j < r; ++j) rk += (lamr[j] > li) || (lamr[j] == li && j < tid);
+            ordr[rk] = tid;
+        }
+        __syncthreads();
+        for (int k = tid; k < L * r; k += nt) {   // Y = X W, columns in descending order
+            const int i = k / r, c = k - i * r;
+            const int src = ordr[c];
+            double acc = 0.0;
+            for (int j = 0; j < r; ++j) acc = fma(X[i * MAX_L_NUC + j], Rb[j * LD32 + src], acc);
+            Y[i * MAX_L_NUC + c] = acc;
+        }
+        __syncthreads();
+        if (tid < r) fv[tid] = lamr[ordr[tid]];
+        __syncthreads();
+        if (tid < r) {
+            const double sig = sqrt(fmax(fv[tid], 0.0));
+            const double c = thr * (w_sv ? w_sv[tid] : 1.0);
+            double f;
+            if (dual) f = (sig > c) ? c / sig : 1.0;
+            else f = (sig > c) ? 1.0 - c / sig : 0.0;
+            if (sv_out) sv_out[tid] = sig;
+            lamr[tid] = f;   // factor of active vector tid (descending)
+        }
+        __syncthreads();
+    }
+    if (sv_out)
+        for (int j = r + tid; j < L; j += nt) sv_out[j] = sqrt(fmax(lam32[order[j]], 0.0));
+    // ---- 4. Mf
+    for (int k = tid; k < L * L; k += nt) {
+        const int i = k / L, m = k - i * L;
+        double acc = dual ? (i == m ? 1.0 : 0.0) : 0.0;
+        for (int c = 0; c < r; ++c) {
+            const double g = dual ? (lamr[c] - 1.0) : lamr[c];
+            acc = fma(g * Y[i * MAX_L_NUC + c], Y[m * MAX_L_NUC + c], acc);
+        }
+        Mf[i * L + m] = acc;
+    }
+}
+
+size_t eig_mixed_smem() {
+    return (size_t)4 * MAX_L_NUC * LD32 * sizeof(float) + (size_t)4 * MAX_L_NUC * LD32 * sizeof(double);
+}
+
+// FP64 plans: the whole Gram matrix is diagonalised by the FP64 Jacobi method;
+// f and Mf as in k_eig_mixed (all eigenpairs are FP64-accurate).
+__global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg, int L,
+                                                  const double* __restrict__ w_sv, double thr, int dual,
+                                                  double* __restrict__ Mf, double* __restrict__ sv_out,
+                                                  int* __restrict__ r_out) {
+    extern __shared__ __align__(16) unsigned char eig_smem[];
+    constexpr int SL = MAX_L_NUC * LD32;
+    double* A = (double*)eig_smem;
+    double* B = A + SL;
+    double* V = B + SL;
+    double* W = V + SL;
+    __shared__ double red[33];
+    __shared__ double cv[MAX_L_NUC], tv[MAX_L_NUC], lam[MAX_L_NUC], fv[MAX_L_NUC];
+    __shared__ int order[MAX_L_NUC];
+    __shared__ signed char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ int flag;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int n = 2;
+    while (n < L) n <<= 1;
+    for (int k = tid; k < n * n; k += nt) {
+        const int i = k / n, j = k - i * n;
+        A[i * LD32 + j] = (i < L && j < L) ? Sg[i * L + j] : 0.0;
+        V[i * LD32 + j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_n<double>(n, A, B, V, W, partner, 1e-17, 1e-18, 1e-16, 40, cv, tv, red, &flag);
+    if (tid < L) lam[tid] = A[tid * LD32 + tid];
+    __syncthreads();
+    if (tid < L) {
+        int rk = 0;
+        const double li = lam[tid];
+        for (int j = 0; j < L; ++j) rk += (lam[j] > li) || (lam[j] == li && j < tid);
+        order[rk] = tid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int r = 0;
+        for (int j = 0; j < L; ++j) {
+            const double sig = sqrt(fmax(lam[order[j]], 0.0));
+            const double c = thr * (w_sv ? w_sv[j] : 1.0);
+            double f;
+            if (dual) f = (sig > c) ? c / sig : 1.0;
+            else f = (sig > c) ? 1.0 - c / sig : 0.0;
+            fv[j] = f;
+            if (sv_out) sv_out[j] = sig;
+            if (sig > c) r = j + 1;
+        }
+        if (r_out) *r_out = r;
+    }
+    __syncthreads();
+    for (int k = tid; k < L * L; k += nt) {
+        const int i = k / L, m = k - i * L;
+        double acc = 0.0;
+        for (int j = 0; j < L; ++j) acc = fma(V[i * LD32 + order[j]] * fv[j], V[m * LD32 + order[j]], acc);
+        Mf[i * L + m] = acc;
+    }
+}
+
+hs_status eig_f64_launch(const double* S, int L, const double* w_sv, double thr, int dual, double* Mf,
+                         double* sv_out, int* r_out, cudaStream_t s) {
+    const size_t sm = (size_t)4 * MAX_L_NUC * LD32 * sizeof(double);
+    k_eig_f64<<<1, EIG_T, sm, s>>>(S, L, w_sv, thr, dual, Mf, sv_out, r_out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status eig_init() {
+    static bool done = false;
+    if (done) return HS_OK;
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_eig_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)eig_mixed_smem()));
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_eig_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(4 * MAX_L_NUC * LD32 * sizeof(double))));
+    done = true;
+    return HS_OK;
+}
+
+hs_status eig_mixed_launch(const double* S, int L, const double* w_sv, double thr, int dual,
+                           double* Mf, double* sv_out, float* warm, int* r_out, cudaStream_t s) {
+    k_eig_mixed<<<1, EIG_T, eig_mixed_smem(), s>>>(S, L, w_sv, thr, dual, Mf, sv_out, warm, r_out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+}  // namespace hs

@@ -29,110 +29,113 @@ template <typename R> struct FftArgs {
     const R* cxs;      // Z scale along x (nx)
     const R* cys;      // Z scale along y (ny)
     int K, G, n8, rlast, npass;
+    int lgK, lgG;      // log2 K, log2 G
     int nx, ny, Kx, Ky;
+    int lgny, lgKx;    // log2 ny, log2 Kx
 };
 
+// A line is a row (l, iy) of the row modes or a column (l, kx) of the column
+// modes; la = channel, lb = iy or kx.
 template <typename R, int MODE>
-__device__ __forceinline__ Cx<R> fft_load(const FftArgs<R>& a, int line, int k) {
+__device__ __forceinline__ void line_of(const FftArgs<R>& a, int line, int& la, int& lb) {
+    if (MODE == COL_FWD || MODE == COL_INV) {
+        la = line >> a.lgKx;
+        lb = line & (a.Kx - 1);
+    } else {
+        la = line >> a.lgny;
+        lb = line & (a.ny - 1);
+    }
+}
+
+template <typename R, int MODE>
+__device__ __forceinline__ Cx<R> fft_load(const FftArgs<R>& a, int la, int lb, int k) {
     typedef Cx<R> CT;
-    if (MODE == ROW_FWD) {
-        const int l = line / a.ny, iy = line - l * a.ny;
+    if (MODE == ROW_FWD) {   // Z: pad and scale
         const int h = a.nx >> 1;
         int ix;
         if (k < h) ix = k + h;
         else if (k >= a.Kx - h) ix = k - a.Kx + h;
         else return cx<R>(0, 0);
         const R* X = (const R*)a.in;
-        return cx<R>(a.cys[iy] * a.cxs[ix] * X[((int64_t)l * a.ny + iy) * a.nx + ix], (R)0);
-    } else if (MODE == COL_FWD) {
-        const int cpb = a.Kx;   // line = l * Kx + kx
-        const int l = line / cpb, kx = line - l * cpb;
+        return cx<R>(a.cys[lb] * a.cxs[ix] * X[((int64_t)la * a.ny + lb) * a.nx + ix], (R)0);
+    } else if (MODE == COL_FWD) {   // only the ny image rows are nonzero
         const int h = a.ny >> 1;
         int iy;
         if (k < h) iy = k + h;
         else if (k >= a.Ky - h) iy = k - a.Ky + h;
         else return cx<R>(0, 0);
-        const CT* T = (const CT*)a.in;
-        return T[((int64_t)l * a.ny + iy) * a.Kx + kx];
+        return ((const CT*)a.in)[((int64_t)la * a.ny + iy) * a.Kx + lb];
     } else if (MODE == COL_INV) {
-        const int l = line / a.Kx, kx = line - l * a.Kx;
-        const CT* Gd = (const CT*)a.in;
-        return Gd[((int64_t)l * a.Ky + k) * a.Kx + kx];
+        return ((const CT*)a.in)[((int64_t)la * a.Ky + k) * a.Kx + lb];
     } else {   // ROW_INV
-        const int l = line / a.ny, iy = line - l * a.ny;
-        const CT* T = (const CT*)a.in;
-        return T[((int64_t)l * a.ny + iy) * a.Kx + k];
+        return ((const CT*)a.in)[((int64_t)la * a.ny + lb) * a.Kx + k];
     }
 }
 
 template <typename R, int MODE>
-__device__ __forceinline__ void fft_store(const FftArgs<R>& a, int line, int k, Cx<R> v) {
+__device__ __forceinline__ void fft_store(const FftArgs<R>& a, int la, int lb, int k, Cx<R> v) {
     typedef Cx<R> CT;
     if (MODE == ROW_FWD) {
-        CT* T = (CT*)a.out;
-        T[(int64_t)line * a.Kx + k] = v;   // line = l * ny + iy
+        ((CT*)a.out)[((int64_t)la * a.ny + lb) * a.Kx + k] = v;
     } else if (MODE == COL_FWD) {
-        const int l = line / a.Kx, kx = line - l * a.Kx;
-        CT* Gd = (CT*)a.out;
-        Gd[((int64_t)l * a.Ky + k) * a.Kx + kx] = v;
-    } else if (MODE == COL_INV) {
-        const int l = line / a.Kx, kx = line - l * a.Kx;
+        ((CT*)a.out)[((int64_t)la * a.Ky + k) * a.Kx + lb] = v;
+    } else if (MODE == COL_INV) {   // keep the ny image rows
         const int h = a.ny >> 1;
         int iy;
         if (k < h) iy = k + h;
         else if (k >= a.Ky - h) iy = k - a.Ky + h;
         else return;
-        CT* T = (CT*)a.out;
-        T[((int64_t)l * a.ny + iy) * a.Kx + kx] = v;
+        ((CT*)a.out)[((int64_t)la * a.ny + iy) * a.Kx + lb] = v;
     } else {   // ROW_INV: crop, scale, real part
-        const int l = line / a.ny, iy = line - l * a.ny;
         const int h = a.nx >> 1;
         int ix;
         if (k < h) ix = k + h;
         else if (k >= a.Kx - h) ix = k - a.Kx + h;
         else return;
-        R* X = (R*)a.out;
-        X[((int64_t)l * a.ny + iy) * a.nx + ix] = a.cys[iy] * a.cxs[ix] * v.x;
+        ((R*)a.out)[((int64_t)la * a.ny + lb) * a.nx + ix] = a.cys[lb] * a.cxs[ix] * v.x;
     }
 }
 
-// One Stockham pass of radix RAD over the CTA's G lines: every thread owns
-// 8 / RAD butterflies (8 operands, all in registers).
-template <typename R, int DIR, int MODE, int RAD>
-__device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int Ns, bool first,
+// One Stockham pass of radix RAD (LGR = log2 RAD) over the CTA's G lines:
+// every thread owns 8 / RAD butterflies (8 operands, all in registers).
+template <typename R, int DIR, int MODE, int RAD, int LGR>
+__device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgNs, bool first,
                                          bool last, int line0) {
     typedef Cx<R> CT;
     constexpr bool COLS = (MODE == COL_FWD || MODE == COL_INV);
     constexpr int PER = 8 / RAD;
     const int K = a.K, G = a.G;
     const int nthr = blockDim.x, tid = threadIdx.x;
-    const int nb = K / RAD;
+    const int lgnb = a.lgK - LGR;
+    const int nb = 1 << lgnb;
+    const int lgstep = a.lgK - lgNs - LGR;
     CT v[8];
     int gs[PER], js[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int w = tid + i * nthr;
-        const int g = COLS ? (w % G) : (w / nb);
-        const int j = COLS ? (w / G) : (w % nb);
+        const int g = COLS ? (w & (G - 1)) : (w >> lgnb);
+        const int j = COLS ? (w >> a.lgG) : (w & (nb - 1));
         gs[i] = g;
         js[i] = j;
+        int la = 0, lb = 0;
+        if (first) line_of<R, MODE>(a, line0 + g, la, lb);
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
             const int k = j + r * nb;
-            v[i * RAD + r] = first ? fft_load<R, MODE>(a, line0 + g, k)
+            v[i * RAD + r] = first ? fft_load<R, MODE>(a, la, lb, k)
                                    : sm[COLS ? (k * G + g) : (g * K + k)];
         }
     }
     if (!first) __syncthreads();   // every read of this pass precedes any write
-    const int step = K / (Ns * RAD);
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int j = js[i];
-        const int kk = j % Ns;
+        const int kk = j & ((1 << lgNs) - 1);
         CT* u = v + i * RAD;
 #pragma unroll
         for (int r = 1; r < RAD; ++r) {
-            CT t = a.tw[kk * r * step];
+            CT t = a.tw[(kk * r) << lgstep];
             if (DIR > 0) t.y = -t.y;
             u[r] = cmul(u[r], t);
         }
@@ -145,12 +148,14 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int Ns,
             u[1] = csub(u[0], u[1]);
             u[0] = t0;
         }
-        const int base = (j / Ns) * Ns * RAD + kk;
+        const int base = ((j >> lgNs) << (lgNs + LGR)) + kk;
         const int g = gs[i];
+        int la = 0, lb = 0;
+        if (last) line_of<R, MODE>(a, line0 + g, la, lb);
 #pragma unroll
         for (int r = 0; r < RAD; ++r) {
-            const int k = base + r * Ns;
-            if (last) fft_store<R, MODE>(a, line0 + g, k, u[r]);
+            const int k = base + (r << lgNs);
+            if (last) fft_store<R, MODE>(a, la, lb, k, u[r]);
             else sm[COLS ? (k * G + g) : (g * K + k)] = u[r];
         }
     }
@@ -159,22 +164,22 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int Ns,
 
 // DIR = -1: forward transform (exp(-2 pi i kn / K)); DIR = +1: unnormalised inverse.
 template <typename R, int DIR, int MODE>
-__global__ void __launch_bounds__(1024) k_fft(FftArgs<R> a) {
+__global__ void __launch_bounds__(512, 2) k_fft(FftArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<R>* sm = reinterpret_cast<Cx<R>*>(smem_raw);
     const int line0 = blockIdx.x * a.G;
-    int Ns = 1;
+    int lgNs = 0;
     for (int pass = 0; pass < a.npass; ++pass) {
         const bool first = (pass == 0), last = (pass == a.npass - 1);
         if (pass < a.n8) {
-            fft_pass<R, DIR, MODE, 8>(a, sm, Ns, first, last, line0);
-            Ns *= 8;
+            fft_pass<R, DIR, MODE, 8, 3>(a, sm, lgNs, first, last, line0);
+            lgNs += 3;
         } else if (a.rlast == 4) {
-            fft_pass<R, DIR, MODE, 4>(a, sm, Ns, first, last, line0);
-            Ns *= 4;
+            fft_pass<R, DIR, MODE, 4, 2>(a, sm, lgNs, first, last, line0);
+            lgNs += 2;
         } else {
-            fft_pass<R, DIR, MODE, 2>(a, sm, Ns, first, last, line0);
-            Ns *= 2;
+            fft_pass<R, DIR, MODE, 2, 1>(a, sm, lgNs, first, last, line0);
+            lgNs += 1;
         }
     }
 }
@@ -204,9 +209,18 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
     a.K = K;
     a.tw = (const Cx<R>*)(cols ? p->twy : p->twx);
     radix_plan(K, &a.n8, &a.rlast, &a.npass);
+    auto lg2 = [](int v) {
+        int r = 0;
+        while ((1 << r) < v) ++r;
+        return r;
+    };
+    a.lgK = lg2(K);
+    a.lgny = lg2(p->g.ny);
+    a.lgKx = lg2(p->g.Kx);
     int G, nlines;
     if (cols) {
-        G = 1024 / (K / 8);
+        // 512 threads per CTA so two CTAs share an SM (one loads while the other computes)
+        G = 512 / (K / 8);
         if (G > 16) G = 16;
         if (G > p->g.Kx) G = p->g.Kx;
         nlines = p->g.L * p->g.Kx;
@@ -218,6 +232,7 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
     }
     if (G < 1) G = 1;
     a.G = G;
+    a.lgG = lg2(G);
     const int threads = G * K / 8;
     const size_t smem = (size_t)G * K * sizeof(Cx<R>);
     const int blocks = nlines / G;

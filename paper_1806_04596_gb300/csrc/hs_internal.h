@@ -40,6 +40,8 @@ constexpr int KB_TERMS_F32 = 9;      // polynomial coefficients per unit piece, 
 constexpr int KB_TERMS_F64 = 14;     // ... FP64
 constexpr int GRID_TILE = 32;        // gridding tile side (cells)
 constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumulators)
+constexpr int GRID_CAP = 512;        // most list entries one gridding CTA processes
+constexpr int GRID_AWARPS = 8;       // warps per CTA of the shared-atomic gridding kernel
 constexpr int DEGRID_CHUNK = 256;    // visibilities per degridding CTA
 constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
 
@@ -78,6 +80,11 @@ struct Plan {
     int64_t n_ent = 0;
     int64_t* tile_off = nullptr;       // L * ntiles + 1
     int* tile_ent = nullptr;           // sorted visibility index per (channel, tile) entry
+    void* grid_items = nullptr;        // gridding work items {tix, e0, e1, slot}
+    int64_t n_items = 0;
+    void* grid_merges = nullptr;       // split tiles {tix, slot0, nslot}
+    int64_t n_merges = 0;
+    void* grid_partial = nullptr;      // partial tiles of split tiles (complex, slots x tile)
     void* kbc = nullptr;               // 8 * kb_terms reals
     void* cxs = nullptr;               // nx reals (Z scale along x)
     void* cys = nullptr;               // ny reals
@@ -161,7 +168,14 @@ hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows
                     int dual, void* out, cudaStream_t s);
 hs_status l21_norm(Plan* p, const void* A, const void* w_rows, double* out_dev, cudaStream_t s);
 hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
-                        int dual, void* out, double* sv_out, cudaStream_t s);
+                        int dual, void* out, double* sv_out, float* warm, int* r_out, cudaStream_t s);
+// FP32 plans: mixed-precision eigendecomposition of the Gram matrix (hs_eig.cu).
+// warm: L x L FP32 eigenvectors of the previous call (updated in place) or null.
+hs_status eig_mixed_launch(const double* S, int L, const double* w_sv, double thr, int dual,
+                           double* Mf, double* sv_out, float* warm, int* r_out, cudaStream_t s);
+// FP64 plans: FP64 Jacobi on the whole Gram matrix (hs_eig.cu).
+hs_status eig_f64_launch(const double* S, int L, const double* w_sv, double thr, int dual, double* Mf,
+                         double* sv_out, int* r_out, cudaStream_t s);
 hs_status ball_project(Plan* p, const void* Z, const void* Yd, const double* eps, int dual,
                        void* out, double* rho_out, cudaStream_t s);
 hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const void* D,

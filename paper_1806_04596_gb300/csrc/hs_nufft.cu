@@ -94,13 +94,24 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
     const int Kx = a.g.Kx, Ky = a.g.Ky;
     const CT* G = a.grid + (int64_t)l * Ky * Kx;
     double sq = 0.0;
-    for (int64_t i0 = beg; i0 < end; i0 += 32) {
-        const int64_t iv = i0 + grp;
+    // lane j of a group preloads the coordinates of the group's j-th visibility,
+    // so the 8 coordinate loads of a group are in flight together
+    int pcx = 0, pcy = 0;
+    R pfx = 0, pfy = 0;
+    {
+        const int64_t ip = beg + grp + 32 * j;
+        if (ip < end) VisCoord<R>::get(a.coords, ip, a.g, pcx, pcy, pfx, pfy);
+    }
+#pragma unroll 2
+    for (int it = 0; it < DEGRID_CHUNK / 32; ++it) {
+        const int64_t iv = beg + grp + 32 * it;
         const bool valid = iv < end;
         const int64_t i = valid ? iv : beg;
-        int cxv, cyv;
-        R fx, fy;
-        VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+        const int src = gbase + it;
+        const int cxv = __shfl_sync(0xffffffffu, pcx, src);
+        const int cyv = __shfl_sync(0xffffffffu, pcy, src);
+        const R fx = __shfl_sync(0xffffffffu, pfx, src);
+        const R fy = __shfl_sync(0xffffffffu, pfy, src);
         const int k0x = (cxv - 3) & (Kx - 1);
         const int k0y = (cyv - 3) & (Ky - 1);
         const R pu = horner<R, NC>(c, (R)2 * fx - (R)1);
@@ -154,16 +165,33 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
 }
 
 // ---------------------------------------------------------------- gridding
+// Work item of the gridding kernel: one (channel, tile) list range. Tiles whose
+// list is longer than GRID_CAP entries are split into several items; each
+// writes its partial tile to a slot of the partial buffer and k_grid_merge
+// adds the slots of a tile in a fixed order. Unsplit tiles (slot < 0) write
+// the grid directly.
+struct GridItem {
+    int tix;      // l * ntiles + tile
+    int e0, e1;   // entry range in tile_ent
+    int slot;     // partial slot, or -1
+};
+
 template <typename R, int NC, int MODE, bool KAHAN>
-__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a) {
+__global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const GridItem* __restrict__ items,
+                                                         Cx<R>* __restrict__ partial) {
     typedef Cx<R> CT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = a.g.tx, TY = a.g.ty;
     const int cells = TX * TY;
     CT* acc = reinterpret_cast<CT*>(smem_raw);             // [GRID_WARPS][cells]
     CT* cmp = acc + (size_t)GRID_WARPS * cells;            // [GRID_WARPS][cells] (KAHAN)
-    const int l = blockIdx.y;
-    const int t = blockIdx.x;
+    __shared__ int2 s_k0[GRID_WARPS][32];                  // window start cells of a batch
+    __shared__ CT s_val[GRID_WARPS][32];                   // weighted values of a batch
+    __shared__ R s_phi[GRID_WARPS][32][17];                // 8 x-taps, 8 y-taps per entry
+    const GridItem it = items[blockIdx.x];
+    const int ntiles = a.g.ntx * a.g.nty;
+    const int l = it.tix / ntiles;
+    const int t = it.tix - l * ntiles;
     const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
     const int ty0 = tyi * TY, tx0 = txi * TX;
     const int Kx = a.g.Kx, Ky = a.g.Ky;
@@ -172,8 +200,6 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a) {
         if (KAHAN) cmp[k] = cx<R>(0, 0);
     }
     __syncthreads();
-    const int64_t tix = (int64_t)l * a.g.ntx * a.g.nty + t;
-    const int64_t e0 = a.tile_off[tix], e1 = a.tile_off[tix + 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = lane >> 4, sub = lane & 15;
     R c[NC];
@@ -182,70 +208,87 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a) {
     CT* mine = acc + (size_t)w * cells;
     CT* mcmp = cmp + (size_t)w * cells;
     const int cc = lane & 7, r0 = lane >> 3;
-    for (int64_t e = e0 + 2 * w; e < e1; e += 2 * GRID_WARPS) {
-        const int64_t em = e + half;
-        const bool valid = em < e1;
-        const int64_t i = a.tile_ent[valid ? em : e];
-        int cxv, cyv;
-        R fx, fy;
-        VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
-        const int k0x = (cxv - 3) & (Kx - 1);
-        const int k0y = (cyv - 3) & (Ky - 1);
-        CT val;
-        if (MODE == GIN_CALLER) {
-            val = a.in[a.perm[i]];
-        } else if (MODE == GIN_SORTED) {
-            val = a.in[i];
-        } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho)
-            val = cscale(a.d[i], a.scale[l]);
-            if (a.u) val = cscale(val, sqrt(a.u[i]));
-            const bool home = (k0x / TX == txi) && (k0y / TY == tyi);
-            if (home && valid && sub == 0) a.v[i] = val;
+    // Batches of 32 entries per warp. (1) lane q fetches entry base + q: index,
+    // coordinates, weighted value (all loads of the batch in flight together);
+    // (2) the 16 kernel taps of every entry are evaluated two entries at a time
+    // (16 lanes each) into shared memory; (3) the windows are added one at a time
+    // into the warp's private tile, 32 lanes covering 8 columns x 2 x 4 rows.
+    for (int base = it.e0 + 32 * w; base < it.e1; base += 32 * GRID_WARPS) {
+        const int e = base + lane;
+        const int nb = min(32, it.e1 - base);
+        R fx = 0, fy = 0;
+        if (e < it.e1) {
+            const int64_t i = a.tile_ent[e];
+            int cxv, cyv;
+            VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+            const int k0x = (cxv - 3) & (Kx - 1);
+            const int k0y = (cyv - 3) & (Ky - 1);
+            CT val;
+            if (MODE == GIN_CALLER) {
+                val = a.in[a.perm[i]];
+            } else if (MODE == GIN_SORTED) {
+                val = a.in[i];
+            } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
+                val = cscale(a.d[i], a.scale[l]);
+                if (a.u) val = cscale(val, sqrt(a.u[i]));
+                if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
+            }
+            if (a.w) val = cscale(val, a.w[i]);
+            s_k0[w][lane] = make_int2(k0x, k0y);
+            s_val[w][lane] = val;
         }
-        if (a.w) val = cscale(val, a.w[i]);
-        const R phi = horner<R, NC>(c, (R)2 * (sub < 8 ? fx : fy) - (R)1);
+        for (int k = 0; k < nb; k += 2) {
+            const int src = k + half;
+            const R fxs = __shfl_sync(0xffffffffu, fx, src);
+            const R fys = __shfl_sync(0xffffffffu, fy, src);
+            const R phi = horner<R, NC>(c, (R)2 * (sub < 8 ? fxs : fys) - (R)1);
+            s_phi[w][src][sub] = phi;
+        }
+        __syncwarp();
+        for (int k = 0; k < nb; ++k) {
+            const int2 b0 = s_k0[w][k];
+            const int gx = ((b0.x + cc) & (Kx - 1)) - tx0;
+            if (gx >= 0 && gx < TX) {
+                const CT vv = s_val[w][k];
+                const R pu = s_phi[w][k][cc];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int src = hh * 16;
-            const int bx = __shfl_sync(0xffffffffu, k0x, src);
-            const int by = __shfl_sync(0xffffffffu, k0y, src);
-            const int bv = __shfl_sync(0xffffffffu, (int)valid, src);
-            CT vv;
-            vv.x = __shfl_sync(0xffffffffu, val.x, src);
-            vv.y = __shfl_sync(0xffffffffu, val.y, src);
-            const R pu = __shfl_sync(0xffffffffu, phi, src + cc);
-            const R pv0 = __shfl_sync(0xffffffffu, phi, src + 8 + r0);
-            const R pv1 = __shfl_sync(0xffffffffu, phi, src + 12 + r0);
-            if (!bv) continue;
-            const int gx = ((bx + cc) & (Kx - 1)) - tx0;
-            if (gx < 0 || gx >= TX) continue;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int gy = ((by + r0 + 4 * q) & (Ky - 1)) - ty0;
-                if (gy < 0 || gy >= TY) continue;
-                const R wgt = pu * (q ? pv1 : pv0);
-                const int cell = gy * TX + gx;
-                if (KAHAN) {
-                    CT s = mine[cell], k = mcmp[cell];
-                    const R yr = fma(wgt, vv.x, -k.x), yi = fma(wgt, vv.y, -k.y);
-                    const R tr = s.x + yr, ti = s.y + yi;
-                    k.x = (tr - s.x) - yr;
-                    k.y = (ti - s.y) - yi;
-                    s.x = tr;
-                    s.y = ti;
-                    mine[cell] = s;
-                    mcmp[cell] = k;
-                } else {
-                    CT s = mine[cell];
-                    s.x = fma(wgt, vv.x, s.x);
-                    s.y = fma(wgt, vv.y, s.y);
-                    mine[cell] = s;
+                for (int q = 0; q < 2; ++q) {
+                    const int rr = r0 + 4 * q;
+                    const int gy = ((b0.y + rr) & (Ky - 1)) - ty0;
+                    if (gy < 0 || gy >= TY) continue;
+                    const R wgt = pu * s_phi[w][k][8 + rr];
+                    const int cell = gy * TX + gx;
+                    if (KAHAN) {
+                        CT sm = mine[cell], kk = mcmp[cell];
+                        const R yr = fma(wgt, vv.x, -kk.x), yi = fma(wgt, vv.y, -kk.y);
+                        const R tr = sm.x + yr, ti = sm.y + yi;
+                        kk.x = (tr - sm.x) - yr;
+                        kk.y = (ti - sm.y) - yi;
+                        sm.x = tr;
+                        sm.y = ti;
+                        mine[cell] = sm;
+                        mcmp[cell] = kk;
+                    } else {
+                        CT sm = mine[cell];
+                        sm.x = fma(wgt, vv.x, sm.x);
+                        sm.y = fma(wgt, vv.y, sm.y);
+                        mine[cell] = sm;
+                    }
                 }
             }
         }
+        __syncwarp();
     }
     __syncthreads();
-    CT* Gout = a.grid_out + (int64_t)l * Ky * Kx;
+    CT* Gout;
+    int64_t gstride;
+    if (it.slot < 0) {
+        Gout = a.grid_out + (int64_t)l * Ky * Kx + (int64_t)ty0 * Kx + tx0;
+        gstride = Kx;
+    } else {
+        Gout = partial + (int64_t)it.slot * cells;
+        gstride = TX;
+    }
     for (int k = threadIdx.x; k < cells; k += blockDim.x) {
         CT s = acc[k];
         if (KAHAN) {
@@ -269,7 +312,139 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a) {
             for (int ww = 1; ww < GRID_WARPS; ++ww) s = cadd(s, acc[(size_t)ww * cells + k]);
         }
         const int gy = k / TX, gx = k - gy * TX;
-        Gout[(int64_t)(ty0 + gy) * Kx + tx0 + gx] = s;
+        Gout[(int64_t)gy * gstride + gx] = s;
+    }
+}
+
+// Default gridding kernel: one shared tile per CTA (row stride GRID_TILE + 8
+// complex values) and shared-memory atomic additions. The additions of a
+// window do not wait for one another, so eight warps stream windows without
+// the read-modify-write chain of the private-tile kernel above. A window is
+// added by a whole warp (lanes = 8 columns x 4 rows, two row passes), so the
+// 64 cells of one atomic instruction are distinct. Per batch of 32 entries the
+// column products phi_u(c) v and row weights phi_v(r) are staged in shared
+// memory. The summation order inside a tile is not fixed (results agree to
+// rounding).
+template <typename R> struct GridAW { static constexpr int value = sizeof(R) == 8 ? 4 : GRID_AWARPS; };
+
+template <typename R, int NC, int MODE>
+__global__ void __launch_bounds__(GridAW<R>::value * 32) k_grid_atomic(NufftK<R> a,
+                                                                     const GridItem* __restrict__ items,
+                                                                     Cx<R>* __restrict__ partial) {
+    typedef Cx<R> CT;
+    constexpr int LDT = GRID_TILE + 8;
+    constexpr int AW = GridAW<R>::value;   // warps (static smem stays < 48 KB)
+    __shared__ __align__(16) R tile[GRID_TILE * LDT * 2];
+    __shared__ int2 s_k0[AW][32];          // window start cells
+    __shared__ CT s_pv[AW][32][8];         // phi_u(c) * v
+    __shared__ R s_pw[AW][32][8];          // phi_v(r)
+    const GridItem it = items[blockIdx.x];
+    const int TX = a.g.tx, TY = a.g.ty;
+    const int ntiles = a.g.ntx * a.g.nty;
+    const int l = it.tix / ntiles;
+    const int t = it.tix - l * ntiles;
+    const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
+    const int ty0 = tyi * TY, tx0 = txi * TX;
+    const int Kx = a.g.Kx, Ky = a.g.Ky;
+    for (int k = threadIdx.x; k < GRID_TILE * LDT * 2; k += blockDim.x) tile[k] = (R)0;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = lane >> 4, sub = lane & 15;
+    R c[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - (sub & 7)) * NC + k];
+    const int cc = lane & 7, r0 = lane >> 3;
+    for (int base = it.e0 + 32 * w; base < it.e1; base += 32 * AW) {
+        const int e = base + lane;
+        const int nb = min(32, it.e1 - base);
+        R fx = 0, fy = 0;
+        CT val = cx<R>(0, 0);
+        if (e < it.e1) {
+            const int64_t i = a.tile_ent[e];
+            int cxv, cyv;
+            VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+            const int k0x = (cxv - 3) & (Kx - 1);
+            const int k0y = (cyv - 3) & (Ky - 1);
+            if (MODE == GIN_CALLER) {
+                val = a.in[a.perm[i]];
+            } else if (MODE == GIN_SORTED) {
+                val = a.in[i];
+            } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
+                val = cscale(a.d[i], a.scale[l]);
+                if (a.u) val = cscale(val, sqrt(a.u[i]));
+                if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
+            }
+            if (a.w) val = cscale(val, a.w[i]);
+            s_k0[w][lane] = make_int2(k0x, k0y);
+        }
+        for (int k = 0; k < nb; k += 2) {
+            const int src = k + half;
+            const R fxs = __shfl_sync(0xffffffffu, fx, src);
+            const R fys = __shfl_sync(0xffffffffu, fy, src);
+            const R vxs = __shfl_sync(0xffffffffu, val.x, src);
+            const R vys = __shfl_sync(0xffffffffu, val.y, src);
+            const R phi = horner<R, NC>(c, (R)2 * (sub < 8 ? fxs : fys) - (R)1);
+            if (sub < 8) s_pv[w][src][sub] = cx<R>(phi * vxs, phi * vys);
+            else s_pw[w][src][sub - 8] = phi;
+        }
+        __syncwarp();
+#pragma unroll 2
+        for (int k = 0; k < nb; ++k) {
+            const int2 b0 = s_k0[w][k];
+            const int gx = ((b0.x + cc) & (Kx - 1)) - tx0;
+            if (gx >= 0 && gx < TX) {
+                const CT pv = s_pv[w][k][cc];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int rr = r0 + 4 * q;
+                    const int gy = ((b0.y + rr) & (Ky - 1)) - ty0;
+                    if (gy < 0 || gy >= TY) continue;
+                    const R pw = s_pw[w][k][rr];
+                    R* cell = tile + 2 * (gy * LDT + gx);
+                    atomicAdd(cell, pw * pv.x);
+                    atomicAdd(cell + 1, pw * pv.y);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    CT* Gout;
+    int64_t gstride;
+    if (it.slot < 0) {
+        Gout = a.grid_out + (int64_t)l * Ky * Kx + (int64_t)ty0 * Kx + tx0;
+        gstride = Kx;
+    } else {
+        Gout = partial + (int64_t)it.slot * TX * TY;
+        gstride = TX;
+    }
+    for (int k = threadIdx.x; k < GRID_TILE * GRID_TILE; k += blockDim.x) {
+        const int gy = k >> 5, gx = k & (GRID_TILE - 1);
+        if (gy < TY && gx < TX)
+            Gout[(int64_t)gy * gstride + gx] = cx<R>(tile[2 * (gy * LDT + gx)], tile[2 * (gy * LDT + gx) + 1]);
+    }
+}
+
+// Sum of the partial tiles of every split tile (fixed slot order).
+struct GridMerge {
+    int tix, slot0, nslot;
+};
+
+template <typename R>
+__global__ void k_grid_merge(const GridMerge* __restrict__ merges, const Cx<R>* __restrict__ partial,
+                             Cx<R>* __restrict__ grid, Geo g) {
+    typedef Cx<R> CT;
+    const GridMerge m = merges[blockIdx.x];
+    const int cells = g.tx * g.ty;
+    const int ntiles = g.ntx * g.nty;
+    const int l = m.tix / ntiles, t = m.tix - l * ntiles;
+    const int tyi = t / g.ntx, txi = t - tyi * g.ntx;
+    CT* G = grid + (int64_t)l * g.Ky * g.Kx + (int64_t)(tyi * g.ty) * g.Kx + txi * g.tx;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) {
+        CT s = partial[(int64_t)m.slot0 * cells + k];
+        for (int j = 1; j < m.nslot; ++j) s = cadd(s, partial[(int64_t)(m.slot0 + j) * cells + k]);
+        const int gy = k / g.tx, gx = k - gy * g.tx;
+        G[(int64_t)gy * g.Kx + gx] = s;
     }
 }
 
@@ -322,14 +497,26 @@ hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s) {
 template <typename R, int NC, int MODE, bool KAHAN>
 static hs_status grid_launch(Plan* p, NufftK<R>& k, cudaStream_t s) {
     const size_t smem = (size_t)GRID_WARPS * p->g.tx * p->g.ty * sizeof(Cx<R>) * (KAHAN ? 2 : 1);
-    dim3 grd((unsigned)p->ntiles(), p->g.L);
-    k_grid<R, NC, MODE, KAHAN><<<grd, GRID_WARPS * 32, smem, s>>>(k);
+    if (p->n_items == 0) return HS_OK;
+    if (KAHAN)
+        k_grid<R, NC, MODE, KAHAN><<<(unsigned)p->n_items, GRID_WARPS * 32, smem, s>>>(
+            k, (const GridItem*)p->grid_items, (Cx<R>*)p->grid_partial);
+    else
+        k_grid_atomic<R, NC, MODE><<<(unsigned)p->n_items, GridAW<R>::value * 32, 0, s>>>(
+            k, (const GridItem*)p->grid_items, (Cx<R>*)p->grid_partial);
     HS_CHECK_LAUNCH();
+    if (p->n_merges > 0) {
+        k_grid_merge<R><<<(unsigned)p->n_merges, 256, 0, s>>>((const GridMerge*)p->grid_merges,
+                                                            (const Cx<R>*)p->grid_partial,
+                                                            (Cx<R>*)p->grid, p->g);
+        HS_CHECK_LAUNCH();
+    }
     return HS_OK;
 }
 
 template <typename R, int NC, int MODE, bool KAHAN> static hs_status grid_attr() {
     const int smem = GRID_WARPS * GRID_TILE * GRID_TILE * (int)sizeof(Cx<R>) * (KAHAN ? 2 : 1);
+    static_assert(sizeof(GridItem) == 16 && sizeof(GridMerge) == 12, "plan-side layout");
     HS_CHECK_CUDA(cudaFuncSetAttribute(k_grid<R, NC, MODE, KAHAN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return HS_OK;
@@ -348,6 +535,9 @@ hs_status nufft_init() {
     HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_CALLER, false>()));
     HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_SORTED, false>()));
     HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_PD, false>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_CALLER, true>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_SORTED, true>()));
+    HS_TRY((grid_attr<double, KB_TERMS_F64, GIN_PD, true>()));
     done = true;
     return HS_OK;
 }
@@ -373,6 +563,7 @@ hs_status grid(Plan* p, const GridArgs& a, cudaStream_t s) {
         if (p->flags & HS_PLAN_COMPENSATED) return grid_t<float, KB_TERMS_F32, true>(p, a, s);
         return grid_t<float, KB_TERMS_F32, false>(p, a, s);
     }
+    if (p->flags & HS_PLAN_COMPENSATED) return grid_t<double, KB_TERMS_F64, true>(p, a, s);
     return grid_t<double, KB_TERMS_F64, false>(p, a, s);
 }
 

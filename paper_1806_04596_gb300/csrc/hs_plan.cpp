@@ -26,6 +26,7 @@ hs_status dwt_init();
 hs_status fft_init();
 hs_status nufft_init();
 hs_status prox_init();
+hs_status eig_init();
 int64_t gram_part_doubles(int L);
 
 hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
@@ -225,6 +226,32 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
     }
     HS_TRY(upload(p, (void**)&p->tile_off, toff));
     HS_TRY(upload(p, (void**)&p->tile_ent, ent));
+    if (p->n_ent >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "too many gridding list entries");
+    // work items: lists longer than GRID_CAP are split; split tiles are merged
+    {
+        std::vector<int> items, merges;
+        int slots = 0;
+        for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
+            const int64_t a = toff[tix], b = toff[tix + 1];
+            const int64_t n = b - a;
+            const int parts = n <= GRID_CAP ? 1 : (int)((n + GRID_CAP - 1) / GRID_CAP);
+            if (parts == 1) {
+                items.insert(items.end(), {(int)tix, (int)a, (int)b, -1});
+            } else {
+                merges.insert(merges.end(), {(int)tix, slots, parts});
+                for (int k = 0; k < parts; ++k) {
+                    const int64_t e0 = a + n * k / parts, e1 = a + n * (k + 1) / parts;
+                    items.insert(items.end(), {(int)tix, (int)e0, (int)e1, slots + k});
+                }
+                slots += parts;
+            }
+        }
+        p->n_items = (int64_t)items.size() / 4;
+        p->n_merges = (int64_t)merges.size() / 3;
+        HS_TRY(upload(p, &p->grid_items, items));
+        HS_TRY(upload(p, &p->grid_merges, merges));
+        HS_TRY(plan_alloc(p, &p->grid_partial, (size_t)std::max(slots, 1) * g.tx * g.ty * p->csize()));
+    }
     HS_TRY(upload(p, (void**)&p->off_d, p->off_h));
 
     // tables
@@ -284,8 +311,8 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
     if (out == nullptr) return fail(HS_ERR_ARG, "out is null");
     *out = nullptr;
     if (vis_offsets == nullptr) return fail(HS_ERR_ARG, "vis_offsets is null");
-    if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 8192 || ny > 8192)
-        return fail(HS_ERR_ARG, "nx, ny must be powers of two in [16, 8192] (got %d x %d)", nx, ny);
+    if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 2048 || ny > 2048)
+        return fail(HS_ERR_ARG, "nx, ny must be powers of two in [16, 2048] (got %d x %d)", nx, ny);
     if (L < 1 || L > 1024) return fail(HS_ERR_ARG, "L must be in [1, 1024] (got %d)", L);
     if (oversample != 2) return fail(HS_ERR_ARG, "oversample must be 2 (got %d)", oversample);
     if (J != 8) return fail(HS_ERR_ARG, "J must be 8 (got %d)", J);
@@ -298,6 +325,7 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
     HS_TRY(fft_init());
     HS_TRY(nufft_init());
     HS_TRY(prox_init());
+    HS_TRY(eig_init());
     std::unique_ptr<Plan> p(new Plan());
     p->prec = prec;
     p->flags = flags;

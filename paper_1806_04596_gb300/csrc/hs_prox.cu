@@ -5,9 +5,9 @@
 //  l2 ball   per-channel projection onto B(y_l, eps_l) (functions g_l), norms
 //            accumulated in FP64 as deterministic per-CTA partial sums.
 //  nuclear   Eq. "prox-L*" through the L x L Gram matrix S = Z^T Z (per-tile
-//            products, FP64 combine), a cyclic Jacobi eigendecomposition of S in
-//            FP64 in one CTA (round-robin parallel ordering), and the apply
-//            Z V diag(f) V^T with f the per-singular-value factor.
+//            products, FP64 combine), its eigendecomposition in one CTA
+//            (hs_eig.cu), and the apply Z V diag(f) V^T with f the
+//            per-singular-value factor.
 //  primal    steps 20-23: G = k1 P + k2 A~ + k3 Phi^dagger v, X = P_+(X - tau G),
 //            X~ = 2 X - X_prev, beta partial sums.
 #include <cmath>
@@ -285,142 +285,6 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int L, do
     }
 }
 
-// Cyclic Jacobi eigendecomposition of the symmetric L x L matrix S (FP64, one
-// CTA), parallel round-robin ordering: each round applies n/2 disjoint
-// rotations, (c, s) from the symmetric Schur decomposition of the 2 x 2 block
-// (Golub & Van Loan, Alg. 8.4.1). Then, with the eigenvalues sorted in
-// descending order, sigma_j = sqrt(max(lambda_j, 0)) and
-//   dual: f_j = min(1, thr w_j / sigma_j) (1 when sigma_j = 0)
-//   prox: f_j = max(0, 1 - thr w_j / sigma_j) (0 when sigma_j = 0),
-// and writes Mf = V diag(f) V^T (L x L) and the singular values.
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ S, int L,
-                                                 const double* __restrict__ w_sv, double thr,
-                                                 int dual, double* __restrict__ Mf,
-                                                 double* __restrict__ sv_out, int max_sweeps) {
-    constexpr int LD = MAX_L_NUC + 1;
-    extern __shared__ __align__(16) double jac_smem[];
-    double* A = jac_smem;                  // MAX_L_NUC * LD
-    double* V = jac_smem + MAX_L_NUC * LD;   // MAX_L_NUC * LD
-    __shared__ double cs[MAX_L_NUC / 2], sn[MAX_L_NUC / 2];
-    __shared__ int pp[MAX_L_NUC / 2], qq[MAX_L_NUC / 2];
-    __shared__ double red[32];
-    __shared__ double fvec[MAX_L_NUC];
-    __shared__ int order[MAX_L_NUC];
-    __shared__ int done;
-    const int n = (L + 1) & ~1;   // even size, padded with a zero row/column
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = tid; k < n * n; k += nt) {
-        const int i = k / n, j = k - i * n;
-        A[i * LD + j] = (i < L && j < L) ? S[i * L + j] : 0.0;
-        V[i * LD + j] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int k = tid; k < n * n; k += nt) {
-            const int i = k / n, j = k - i * n;
-            const double a = A[i * LD + j];
-            if (i == j) dia += a * a;
-            else off += a * a;
-        }
-        off = block_sum(off, red);
-        dia = block_sum(dia, red);
-        if (tid == 0) done = !(off > 1e-32 * dia) ? 1 : 0;
-        __syncthreads();
-        if (done) break;
-        for (int r = 0; r < n - 1; ++r) {
-            if (tid < n / 2) {
-                int p, q;
-                if (tid == 0) {
-                    p = r;
-                    q = n - 1;
-                } else {
-                    p = (r + tid) % (n - 1);
-                    q = (r - tid + (n - 1)) % (n - 1);
-                }
-                if (p > q) {
-                    const int tmp = p;
-                    p = q;
-                    q = tmp;
-                }
-                const double apq = A[p * LD + q];
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0 &&
-                    fabs(apq) > 1e-300 + 1e-18 * sqrt(fabs(A[p * LD + p] * A[q * LD + q]))) {
-                    const double tau = (A[q * LD + q] - A[p * LD + p]) / (2.0 * apq);
-                    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
-                }
-                cs[tid] = c;
-                sn[tid] = s;
-                pp[tid] = p;
-                qq[tid] = q;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (int k = tid; k < (n / 2) * n; k += nt) {
-                const int pr = k / n, col = k - pr * n;
-                const int p = pp[pr], q = qq[pr];
-                const double c = cs[pr], s = sn[pr];
-                const double ap = A[p * LD + col], aq = A[q * LD + col];
-                A[p * LD + col] = c * ap - s * aq;
-                A[q * LD + col] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns: A <- A J, V <- V J
-            for (int k = tid; k < (n / 2) * n; k += nt) {
-                const int pr = k / n, row = k - pr * n;
-                const int p = pp[pr], q = qq[pr];
-                const double c = cs[pr], s = sn[pr];
-                const double ap = A[row * LD + p], aq = A[row * LD + q];
-                A[row * LD + p] = c * ap - s * aq;
-                A[row * LD + q] = s * ap + c * aq;
-                const double vp = V[row * LD + p], vq = V[row * LD + q];
-                V[row * LD + p] = c * vp - s * vq;
-                V[row * LD + q] = s * vp + c * vq;
-            }
-            __syncthreads();
-            if (tid < n / 2) {   // the rotated pair is now decoupled
-                const int p = pp[tid], q = qq[tid];
-                if (sn[tid] != 0.0) {
-                    A[p * LD + q] = 0.0;
-                    A[q * LD + p] = 0.0;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (tid == 0) {   // descending eigenvalue order (selection sort, L <= 64)
-        for (int i = 0; i < L; ++i) order[i] = i;
-        for (int i = 0; i < L; ++i) {
-            int best = i;
-            for (int j = i + 1; j < L; ++j)
-                if (A[order[j] * LD + order[j]] > A[order[best] * LD + order[best]]) best = j;
-            const int tmp = order[i];
-            order[i] = order[best];
-            order[best] = tmp;
-        }
-        for (int j = 0; j < L; ++j) {
-            const double lam = A[order[j] * LD + order[j]];
-            const double sig = sqrt(lam > 0.0 ? lam : 0.0);
-            const double lamb = thr * (w_sv ? w_sv[j] : 1.0);
-            double f;
-            if (dual) f = (sig > lamb) ? lamb / sig : 1.0;
-            else f = (sig > lamb) ? 1.0 - lamb / sig : 0.0;
-            fvec[j] = f;
-            if (sv_out) sv_out[j] = sig;
-        }
-    }
-    __syncthreads();
-    for (int k = tid; k < L * L; k += nt) {
-        const int i = k / L, m = k - i * L;
-        double acc = 0.0;
-        for (int j = 0; j < L; ++j) acc += V[i * LD + order[j]] * fvec[j] * V[m * LD + order[j]];
-        Mf[i * L + m] = acc;
-    }
-}
-
 // out[:, m] = sum_i Z[:, i] Mf[i, m] with Z = X + Xa, one thread per pixel,
 // the pixel's L values in registers, Mf broadcast from shared memory. In FP32
 // the FP64 factor matrix is carried as two FP32 parts (hi + lo), so that its
@@ -481,7 +345,8 @@ static hs_status lowrank_apply_t(Plan* p, const void* X, const void* Xa, void* o
 }
 
 hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
-                        int dual, void* out, double* sv_out, cudaStream_t s) {
+                        int dual, void* out, double* sv_out, float* warm, int* r_out,
+                        cudaStream_t s) {
     const int L = p->g.L;
     if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "nuclear prox: L = %d exceeds %d", L, MAX_L_NUC);
     const int64_t N = p->N();
@@ -494,21 +359,18 @@ hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* 
     HS_CHECK_LAUNCH();
     k_gram_reduce<<<P, 128, 0, s>>>(gpart, GRAM_CTAS, L, p->gram);
     HS_CHECK_LAUNCH();
-    const size_t jsm = 2 * sizeof(double) * MAX_L_NUC * (MAX_L_NUC + 1);
-    k_jacobi<<<1, 1024, jsm, s>>>(p->gram, L, w_sv, thr, dual, p->eigf, sv_out, 40);
-    HS_CHECK_LAUNCH();
+    if (p->prec == HS_F32) {
+        // FP32 Jacobi (warm-started) + FP64 refinement of the active eigenpairs
+        HS_TRY(eig_mixed_launch(p->gram, L, w_sv, thr, dual, p->eigf, sv_out, warm, r_out, s));
+    } else {
+        // FP64 plans: cyclic Jacobi entirely in FP64
+        HS_TRY(eig_f64_launch(p->gram, L, w_sv, thr, dual, p->eigf, sv_out, r_out, s));
+    }
     if (p->prec == HS_F32) return lowrank_apply_t<float>(p, X, Xadd, out, s);
     return lowrank_apply_t<double>(p, X, Xadd, out, s);
 }
 
-hs_status prox_init() {
-    static bool done = false;
-    if (done) return HS_OK;
-    HS_CHECK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(2 * sizeof(double) * MAX_L_NUC * (MAX_L_NUC + 1))));
-    done = true;
-    return HS_OK;
-}
+hs_status prox_init() { return HS_OK; }
 
 int64_t gram_part_doubles(int L) { return (int64_t)(L * (L + 1) / 2) * GRAM_CTAS; }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "hs_pd_get": ([_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "hs_pd_iterations": ([_P, C.POINTER(C.c_int64)], C.c_int),
     "hs_pd_graph_kernels": ([_P, C.POINTER(C.c_int)], C.c_int),
+    "hs_pd_nuclear_info": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int), _P], C.c_int),
     "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
 }
@@ -287,6 +288,13 @@ class PDState:
         rho = (C.c_double * self.plan.L)()
         _check("hs_pd_get", load().hs_pd_get(self.h, _ptr(X), C.byref(beta), rho, _stream()))
         return X, beta.value, np.array(rho[:])
+
+    def nuclear_info(self):
+        """(singular values of P + X~ at the last step, count above the threshold)."""
+        sv = (C.c_double * self.plan.L)()
+        n = C.c_int()
+        _check("hs_pd_nuclear_info", load().hs_pd_nuclear_info(self.h, sv, C.byref(n), _stream()))
+        return np.array(sv[:]), n.value
 
     @property
     def graph_kernels(self) -> int:

@@ -35,11 +35,12 @@ def _setup(inp, prec, levels=4, U=None):
     return prob, prm
 
 
-def _gpu_state(inp, prob, prm, prec, U=None, use_nuclear=True, use_l21=True):
+def _gpu_state(inp, prob, prm, prec, U=None, use_nuclear=True, use_l21=True, compensated=False):
     import torch
     from paper_1806_04596_gb300 import hypersara as hs
     plan = hs.Plan(inp.nx, inp.ny, inp.offsets, dev(inp.uv, prec),
-                   precond=None if U is None else dev(U, prec), levels=prm.levels, prec=prec)
+                   precond=None if U is None else dev(U, prec), levels=prm.levels, prec=prec,
+                   compensated=compensated)
     st = hs.PDState(plan, dev(prob.y, prec, True), torch.tensor(prob.eps, dtype=torch.float64,
                                                                 device="cuda"),
                     tau=prm.tau, kappa1=prm.kappa1, kappa2=prm.kappa2, kappa3=prm.kappa3, mu=prm.mu,
@@ -82,15 +83,20 @@ def test_pd_fp32_matches_oracle_snr_c1():
 
 
 def test_pd_graph_equals_eager():
+    """With the fixed-order (compensated) gridding the replayed graph reproduces
+    the eager launches bitwise; with shared-atomic gridding to rounding."""
     inp = synth.make_inputs(1, n=64, L=3, M=(800, 1500), seed=77)
     prob, prm = _setup(inp, "f32")
-    _, s1 = _gpu_state(inp, prob, prm, "f32")
-    _, s2 = _gpu_state(inp, prob, prm, "f32")
+    _, s1 = _gpu_state(inp, prob, prm, "f32", compensated=True)
+    _, s2 = _gpu_state(inp, prob, prm, "f32", compensated=True)
     s1.solve(7, graph=True)
     s2.solve(7, graph=False)
     a = host(s1.get()[0])
     b = host(s2.get()[0])
     assert np.array_equal(a, b)
+    _, s3 = _gpu_state(inp, prob, prm, "f32")
+    s3.solve(7, graph=True)
+    assert rel(host(s3.get()[0]), a) <= 1e-5
 
 
 def test_pd_fp64_with_preconditioner_and_priors_off():
