@@ -14,8 +14,10 @@ Printed (one JSON line, rank 0):
              uploads the data y from pinned host memory (set_data) and reads the
              iteration's beta and per-channel residual norms back
   phi_vis_per_s   Phi + Phi^dagger throughput (visibilities / s over all channels)
-  roofline   Phi + Phi^dagger pair against the measured HBM copy bandwidth, with
-             algorithmic bytes 2 (68 N + 16 M) L per pair (FP32)
+  roofline   the slowest stage of the iteration, launched alone and timed with
+             CUDA events on its stream, against the measured HBM copy bandwidth
+             (algorithmic bytes per launch as listed in `stages`); `phi_pair`
+             gives the same for Phi + Phi^dagger, 2 (68 N + 16 M) L bytes (FP32)
   fp64       the plain FP64 GPU form of the same iteration (iterations / s)
   cpu_baseline   the FP64 NumPy oracle on a bounded sample of the workload
 
@@ -250,10 +252,11 @@ def run_ours(a):
     asnr = float(np.mean([20 * np.log10(np.linalg.norm(inp.truth[l]) /
                                         np.linalg.norm(inp.truth[l] - Xh[l])) for l in range(L)]))
 
-    # Phi + Phi^dagger throughput and roofline
+    # Phi + Phi^dagger throughput
     Xin = P.truth.clone()
     Y = plan.vis()
     Xo = plan.cube()
+    A9 = plan.cube(9)
     for _ in range(3):
         plan.phi_fwd(Xin, Y)
         plan.phi_adj(Y, Xo)
@@ -271,14 +274,29 @@ def run_ours(a):
     torch.cuda.synchronize()
     pair_ms = f0.elapsed_time(f1) / reps
     phi_vis = M / (pair_ms / 1e3)
-    alg_bytes = 2 * (68 * N + 16 * (M / L)) * L
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])
         peak_src = "measured"
     except Exception:
         hbm, peak_src = 6800.0, "fallback"
-    achieved = alg_bytes / (pair_ms / 1e3) / 1e9
+    pair_bytes = 2 * (68 * N + 16 * (M / L)) * L
+    pair_gbs = pair_bytes / (pair_ms / 1e3) / 1e9
+
+    # every stage of the iteration launched alone (CUDA events on this stream);
+    # algorithmic bytes per launch (FP32): spectrum 32 B / grid cell (4N cells
+    # per channel), image 4 B / pixel, 16 B per visibility (coordinates + value)
+    NL = N * L
+    stage_bytes = {"fft_fwd": 36 * NL, "degrid": 32 * NL + 16 * M, "grid": 16 * M + 32 * NL,
+                   "fft_adj": 36 * NL, "psi_fwd": 40 * NL, "psi_adj": 40 * NL}
+    stage_io = {"fft_fwd": (Xin, None), "degrid": (None, Y), "grid": (Y, None), "fft_adj": (None, Xo),
+                "psi_fwd": (Xin, A9), "psi_adj": (A9, Xo)}
+    stages = {}
+    for name, (si, so) in stage_io.items():
+        ms_s = plan.time_stage(name, si, so, reps=max(5, a.steps // 2))
+        gbs = stage_bytes[name] / (ms_s / 1e3) / 1e9
+        stages[name] = {"ms": ms_s, "alg_bytes": stage_bytes[name], "GB_s": gbs, "frac": gbs / hbm}
+    dom = max(stages, key=lambda k: stages[k]["ms"])
 
     # end to end through the public API with host buffers
     y_host = P.y.cpu().pin_memory()
@@ -324,10 +342,12 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _workload(a.config),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "kernel": "Phi + Phi^dagger pair (pad+FFT, degrid, grid, inverse FFT+crop)",
-                     "alg_bytes_per_launch": alg_bytes, "peak_source": peak_src},
+        "roofline": {"bound": "hbm", "achieved": stages[dom]["GB_s"], "peak": hbm, "unit": "GB/s",
+                     "frac": stages[dom]["frac"], "traffic": None, "kernel": dom,
+                     "alg_bytes_per_launch": stages[dom]["alg_bytes"], "launch_ms": stages[dom]["ms"],
+                     "peak_source": peak_src},
+        "stages": stages,
+        "phi_pair": {"ms": pair_ms, "alg_bytes": pair_bytes, "GB_s": pair_gbs, "frac": pair_gbs / hbm},
         "phi_vis_per_s": phi_vis, "phi_pair_ms": pair_ms,
         "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -285,6 +285,26 @@ HS_API hs_status hs_pd_nuclear_info(hs_pd_state_t state, double* sv_host, int* a
 /* Number of iterations performed by a state. */
 HS_API hs_status hs_pd_iterations(hs_pd_state_t state, int64_t* out);
 
+/* Stages of the measurement path that hs_time_stage can launch alone. */
+typedef enum {
+    HS_STAGE_FFT_FWD = 0,   /* X (L x ny x nx) -> plan grid: Z, then F (row and column passes) */
+    HS_STAGE_DEGRID = 1,    /* plan grid -> Y (caller order): G Theta */
+    HS_STAGE_GRID = 2,      /* Y (caller order) -> plan grid: G^H Theta^H */
+    HS_STAGE_FFT_ADJ = 3,   /* plan grid -> X: F^H, then Z^T */
+    HS_STAGE_PSI_FWD = 4,   /* X -> A: Psi^dagger */
+    HS_STAGE_PSI_ADJ = 5    /* A -> X: Psi */
+} hs_stage;
+
+/*
+ * hs_time_stage - profiling aid: launches one stage `reps` times on `stream`
+ * and returns in *avg_ms the mean duration per launch, measured with CUDA
+ * events recorded on that stream (synchronises it). `in` / `out` are the
+ * stage's DEVICE input and output as listed in hs_stage (unused ones may be
+ * NULL); stages that read or write "plan grid" use the plan's scratch grid.
+ */
+HS_API hs_status hs_time_stage(hs_plan_t plan, int stage, const void* in, void* out, int reps,
+                               float* avg_ms, void* stream);
+
 /*
  * Host-only helpers (no GPU needed). Used by the plan; exported so that the
  * derived tables can be inspected.

@@ -230,6 +230,60 @@ hs_status hs_norm_l21(hs_plan_t plan, const void* A, const void* w_rows, double*
     return HS_OK;
 }
 
+static hs_status run_stage(Plan* p, int stage, const void* in, void* out, cudaStream_t s) {
+    switch (stage) {
+        case HS_STAGE_FFT_FWD: return fft_forward(p, in, s);
+        case HS_STAGE_DEGRID: {
+            DegridArgs a{};
+            a.mode = DOUT_CALLER;
+            a.out = out;
+            return degrid(p, a, s);
+        }
+        case HS_STAGE_GRID: {
+            GridArgs a{};
+            a.mode = GIN_CALLER;
+            a.in = in;
+            return grid(p, a, s);
+        }
+        case HS_STAGE_FFT_ADJ: return fft_adjoint(p, out, s);
+        case HS_STAGE_PSI_FWD: return dwt_analysis(p, in, out, s);
+        case HS_STAGE_PSI_ADJ: return dwt_synthesis(p, in, out, s);
+        default: return fail(HS_ERR_ARG, "hs_time_stage: unknown stage %d", stage);
+    }
+}
+
+hs_status hs_time_stage(hs_plan_t plan, int stage, const void* in, void* out, int reps, float* avg_ms,
+                        void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (avg_ms == nullptr || reps < 1) return fail(HS_ERR_ARG, "hs_time_stage: need avg_ms, reps >= 1");
+    const bool needs_in = stage == HS_STAGE_FFT_FWD || stage == HS_STAGE_GRID || stage == HS_STAGE_PSI_FWD ||
+                          stage == HS_STAGE_PSI_ADJ;
+    const bool needs_out = stage == HS_STAGE_DEGRID || stage == HS_STAGE_FFT_ADJ ||
+                           stage == HS_STAGE_PSI_FWD || stage == HS_STAGE_PSI_ADJ;
+    if ((needs_in && in == nullptr && plan->p->M_total > 0) || (needs_out && out == nullptr))
+        return fail(HS_ERR_ARG, "hs_time_stage: missing buffer for stage %d", stage);
+    cudaStream_t s = S(stream);
+    Plan* p = plan->p;
+    HS_TRY(run_stage(p, stage, in, out, s));   // warm
+    cudaEvent_t e0, e1;
+    HS_CHECK_CUDA(cudaEventCreate(&e0));
+    HS_CHECK_CUDA(cudaEventCreate(&e1));
+    hs_status st = HS_OK;
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps && st == HS_OK; ++i) st = run_stage(p, stage, in, out, s);
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HS_OK) return st;
+    if (ce != cudaSuccess) return fail(HS_ERR_CUDA, "hs_time_stage: %s", cudaGetErrorString(ce));
+    *avg_ms = ms / reps;
+    return HS_OK;
+}
+
 // splitmix64 followed by Box-Muller: a fixed, documented start vector.
 static uint64_t splitmix64(uint64_t& x) {
     uint64_t z = (x += 0x9E3779B97F4A7C15ull);

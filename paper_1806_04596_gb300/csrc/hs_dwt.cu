@@ -26,155 +26,344 @@ template <typename R> __device__ __forceinline__ R filt(int d, int hg, int j);
 template <> __device__ __forceinline__ float filt<float>(int d, int hg, int j) { return c_filt_f[d][hg][j]; }
 template <> __device__ __forceinline__ double filt<double>(int d, int hg, int j) { return c_filt_d[d][hg][j]; }
 
-// Dirac basis: A[0][l] = X[l] / 3
-template <typename R>
-__global__ void k_scale_copy(const R* __restrict__ in, R* __restrict__ out, int64_t n, R s) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = s * in[i];
-}
-
 constexpr int DQ = 16;                    // coefficients per subband and axis in one tile
 constexpr int DIN = 2 * DQ + MAXF - 2;    // analysis input region side (46)
+constexpr int SIN = DIN + 4;              // its row stride (50: pair loads hit distinct banks)
+constexpr int SRO = 48;                   // row-filtered tile stride: lowpass at 0, highpass at 16
 constexpr int DC = DQ + MAXF / 2 - 1;     // synthesis coefficient region side (23)
+constexpr int SCF = 24;                   // its row stride
+constexpr int SCL = 2 * SCF + 1;          // column-filtered tile stride (x-lowpass at 0, highpass at 24)
+constexpr int FWD_SMEM = DIN * SIN + 2 * DIN * SRO;        // reals
+constexpr int INV_SMEM = 2 * 4 * DC * SCF + 2 * DQ * SCL;  // reals
+static_assert(2 * DQ * (DQ * 2 + 1) <= 2 * DQ * SCL, "output transpose fits the column tile");
 
-// One analysis level for every (wavelet d, channel l). Input: the my x mx block
-// (level 0: X / 3, row stride nx; otherwise the previous level's LL, compact
-// with stride mx, in `src`). The three detail subbands go to A[1+d] at their
-// Mallat positions (stride nx); LL goes to `ll_out` (compact, stride mx / 2),
-// or to A[1+d] at the last level. 256 threads as 8 rows of 32 lanes.
+// Runs CALL(D) for the runtime wavelet index d (0..7) with D a compile-time
+// constant, so every filter loop unrolls with constant taps.
+#define HS_DWT_DISPATCH(d, CALL)  \
+    switch (d) {                  \
+        case 0: CALL(0); break;   \
+        case 1: CALL(1); break;   \
+        case 2: CALL(2); break;   \
+        case 3: CALL(3); break;   \
+        case 4: CALL(4); break;   \
+        case 5: CALL(5); break;   \
+        case 6: CALL(6); break;   \
+        default: CALL(7); break;  \
+    }
+
+// ---- asynchronous global -> shared staging (the halo loads never stall a warp)
+template <typename R> __device__ __forceinline__ void cp_async(R* dst, const R* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename R> __device__ __forceinline__ Cx<R> ld2(const R* p) { return *reinterpret_cast<const Cx<R>*>(p); }
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+// Stages rows [y0, y0 + ry) x columns [x0, x0 + rx) of a periodic block (indices
+// wrapped with the power-of-two masks) into in[r * SIN + c].
 template <typename R>
-__global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ X, const R* __restrict__ src,
-                                                      R* __restrict__ A, R* __restrict__ ll_out, int L,
-                                                      int ny, int nx, int my, int mx, int lev0, int last,
-                                                      R s0) {
-    __shared__ R in[DIN][DIN + 1];
-    __shared__ R ro[DIN][2 * DQ + 1];
+__device__ __forceinline__ void stage_region(R* in, const R* __restrict__ base, int64_t stride, int ymask,
+                                             int xmask, int y0, int x0, int ry, int rx) {
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    for (int r = wy; r < ry; r += 8) {
+        const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
+        for (int c = lane; c < rx; c += 32) cp_async(in + r * SIN + c, row + ((x0 + c) & xmask));
+    }
+    cp_async_commit();
+}
+
+// Analysis along x of wavelet D (F = 2D + 2 taps): thread (r, g) filters input
+// row r into the 4 lowpass and 4 highpass outputs 4g .. 4g + 3, reading the
+// F + 6 inputs they share once, as pairs.
+template <typename R, int D>
+__device__ __forceinline__ void fwd_rows(const R* __restrict__ in, R* __restrict__ ro, int ry, int qx) {
+    constexpr int F = 2 * (D + 1);
+    constexpr int NV = F + 6;
+    const int r = threadIdx.x >> 2, g = threadIdx.x & 3;
+    if (r >= ry || 4 * g >= qx) return;
+    R v[NV];
+    const R* p = in + r * SIN + 8 * g;
+#pragma unroll
+    for (int k = 0; k < NV / 2; ++k) {
+        const Cx<R> t = ld2(p + 2 * k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+    R lo[4], hi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        R a = 0, b = 0;
+#pragma unroll
+        for (int j = 0; j < F; ++j) {
+            a = fma(filt<R>(D, 0, j), v[2 * u + j], a);
+            b = fma(filt<R>(D, 1, j), v[2 * u + j], b);
+        }
+        lo[u] = a;
+        hi[u] = b;
+    }
+    st4(ro + r * SRO + 4 * g, lo[0], lo[1], lo[2], lo[3]);
+    st4(ro + r * SRO + 16 + 4 * g, hi[0], hi[1], hi[2], hi[3]);
+}
+
+// Analysis along y of the row-filtered tile and the subband stores: thread
+// (col, g) makes output rows 2g, 2g + 1 of tile column col (0-15: x-lowpass,
+// 16-31: x-highpass), lowpass and highpass in y, scaled by sc.
+template <typename R, int D>
+__device__ __forceinline__ void fwd_cols(const R* __restrict__ ro, R sc, R* __restrict__ Ad,
+                                         R* __restrict__ LLo, int64_t lls, int nx, int hy, int hx, int k0y,
+                                         int k0x, int qy, int qx) {
+    constexpr int F = 2 * (D + 1);
+    constexpr int NV = F + 2;
+    const int col = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int c = col & 15;
+    const bool xhi = col >= 16;
+    if (c >= qx || 2 * g >= qy) return;
+    R v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = ro[(4 * g + k) * SRO + col];
+    R lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+    for (int j = 0; j < F; ++j) {
+        lo0 = fma(filt<R>(D, 0, j), v[j], lo0);
+        hi0 = fma(filt<R>(D, 1, j), v[j], hi0);
+        lo1 = fma(filt<R>(D, 0, j), v[j + 2], lo1);
+        hi1 = fma(filt<R>(D, 1, j), v[j + 2], hi1);
+    }
+    const int oy = k0y + 2 * g;
+    const bool two = 2 * g + 1 < qy;
+    if (xhi) {
+        R* o = Ad + (int64_t)oy * nx + hx + k0x + c;
+        o[0] = sc * lo0;
+        if (two) o[nx] = sc * lo1;
+    } else {
+        R* o = LLo + (int64_t)oy * lls + k0x + c;
+        o[0] = sc * lo0;
+        if (two) o[lls] = sc * lo1;
+    }
+    R* o = Ad + (int64_t)(hy + oy) * nx + (xhi ? hx : 0) + k0x + c;
+    o[0] = sc * hi0;
+    if (two) o[nx] = sc * hi1;
+}
+
+template <typename R> struct FwdCtx {
+    const R* in;
+    R* ro;
+    R* A;
+    R* ll_out;
+    int64_t N;
+    int L, l, nx, hy, hx, k0y, k0x, qy, qx, last;
+    R sc;
+};
+
+// All eight wavelets of level 0 from the one staged input tile; the
+// row-filtered tile is double-buffered, so one barrier per wavelet suffices.
+template <typename R, int D> __device__ __forceinline__ void fwd_all(const FwdCtx<R>& c) {
+    if constexpr (D < NW) {
+        constexpr int F = 2 * (D + 1);
+        R* rb = c.ro + (D & 1) * DIN * SRO;
+        fwd_rows<R, D>(c.in, rb, 2 * c.qy + F - 2, c.qx);
+        __syncthreads();
+        R* Ad = c.A + ((int64_t)(1 + D) * c.L + c.l) * c.N;
+        R* LLo = c.last ? Ad : c.ll_out + ((int64_t)D * c.L + c.l) * (int64_t)c.hy * c.hx;
+        fwd_cols<R, D>(rb, c.sc, Ad, LLo, c.last ? c.nx : c.hx, c.nx, c.hy, c.hx, c.k0y, c.k0x, c.qy, c.qx);
+        fwd_all<R, D + 1>(c);
+    }
+}
+
+// Level 0 of Psi^dagger for one (output tile, channel): the Dirac block
+// A[0] = X / 3 and the first level of all 8 wavelets. LL goes to the compact
+// buffer ll_out (stride nx / 2), or to A[1+d] when there is a single level.
+template <typename R>
+__global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* __restrict__ A,
+                                                   R* __restrict__ ll_out, int L, int ny, int nx, int last,
+                                                   R sc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* in = reinterpret_cast<R*>(smem_raw);
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int l = blockIdx.y;
+    const int hy = ny >> 1, hx = nx >> 1;
+    const int qy = min(DQ, hy), qx = min(DQ, hx);
+    const int ntx = hx / qx;
+    const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
+    const int k0y = ty * qy, k0x = tx * qx;
+    const int64_t N = (int64_t)ny * nx;
+    stage_region(in, X + l * N, nx, ny - 1, nx - 1, 2 * k0y, 2 * k0x, 2 * qy + MAXF - 2, 2 * qx + MAXF - 2);
+    cp_async_wait<0>();
+    __syncthreads();
+    R* A0 = A + l * N + (int64_t)(2 * k0y) * nx + 2 * k0x;
+    for (int r = wy; r < 2 * qy; r += 8)
+        if (lane < 2 * qx) A0[(int64_t)r * nx + lane] = sc * in[r * SIN + lane];
+    FwdCtx<R> c{in, in + DIN * SIN, A, ll_out, N, L, l, nx, hy, hx, k0y, k0x, qy, qx, last, sc};
+    fwd_all<R, 0>(c);
+}
+
+// One analysis level > 0 for every (wavelet d, channel l): input the previous
+// level's LL (compact my x mx in `src`); details to A[1+d] at their Mallat
+// positions, LL to `ll_out` (compact) or to A[1+d] at the last level.
+template <typename R>
+__global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ src, R* __restrict__ A,
+                                                      R* __restrict__ ll_out, int L, int ny, int nx, int my,
+                                                      int mx, int last) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* in = reinterpret_cast<R*>(smem_raw);
+    R* ro = in + DIN * SIN;
     const int d = blockIdx.y / L, l = blockIdx.y - d * L;
-    const int F = 2 * (d + 1);
     const int hy = my >> 1, hx = mx >> 1;
     const int qy = min(DQ, hy), qx = min(DQ, hx);
     const int ntx = hx / qx;
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int k0y = ty * qy, k0x = tx * qx;
-    const int ry = 2 * qy + F - 2, rx = 2 * qx + F - 2;
     const int64_t N = (int64_t)ny * nx;
-    const R* base;
-    int64_t stride;
-    if (lev0) {
-        base = X + (int64_t)l * N;
-        stride = nx;
-    } else {
-        base = src + ((int64_t)d * L + l) * (int64_t)my * mx;
-        stride = mx;
-    }
-    const R sc = lev0 ? s0 : (R)1;
-    for (int r = wy; r < ry; r += 8) {
-        const R* row = base + (int64_t)((2 * k0y + r) & (my - 1)) * stride;
-        for (int c = lane; c < rx; c += 32) in[r][c] = sc * row[(2 * k0x + c) & (mx - 1)];
-    }
-    __syncthreads();
-    {   // rows: lanes 0-15 row r, lanes 16-31 row r + 1; lane computes both halves
-        const int c = lane & (DQ - 1), rofs = lane >> 4;
-        if (c < qx)
-            for (int r = 2 * wy + rofs; r < ry; r += 16) {
-                R lo = 0, hi = 0;
-                for (int j = 0; j < F; ++j) {
-                    const R v = in[r][2 * c + j];
-                    lo = fma(filt<R>(d, 0, j), v, lo);
-                    hi = fma(filt<R>(d, 1, j), v, hi);
-                }
-                ro[r][c] = lo;
-                ro[r][qx + c] = hi;
-            }
-    }
-    __syncthreads();
+    const R* base = src + ((int64_t)d * L + l) * (int64_t)my * mx;
     R* Ad = A + ((int64_t)(1 + d) * L + l) * N;
     R* LLo = last ? Ad : ll_out + ((int64_t)d * L + l) * (int64_t)hy * hx;
     const int64_t lls = last ? nx : hx;
-    if (lane < 2 * qx) {   // columns + stores: lane = output column of the row-filtered tile
-        const bool xlow = lane < qx;
-        const int ox = xlow ? k0x + lane : hx + k0x + (lane - qx);
-        for (int r = wy; r < qy; r += 8) {
-            R lo = 0, hi = 0;
-            for (int j = 0; j < F; ++j) {
-                const R v = ro[2 * r + j][lane];
-                lo = fma(filt<R>(d, 0, j), v, lo);
-                hi = fma(filt<R>(d, 1, j), v, hi);
+#define HS_FWD(DD)                                                                                       \
+    {                                                                                                    \
+        constexpr int F = 2 * (DD + 1);                                                                  \
+        stage_region(in, base, mx, my - 1, mx - 1, 2 * k0y, 2 * k0x, 2 * qy + F - 2, 2 * qx + F - 2);    \
+        cp_async_wait<0>();                                                                              \
+        __syncthreads();                                                                                 \
+        fwd_rows<R, DD>(in, ro, 2 * qy + F - 2, qx);                                                     \
+        __syncthreads();                                                                                 \
+        fwd_cols<R, DD>(ro, (R)1, Ad, LLo, lls, nx, hy, hx, k0y, k0x, qy, qx);                           \
+    }
+    HS_DWT_DISPATCH(d, HS_FWD)
+#undef HS_FWD
+}
+
+// ---- synthesis
+// Stages the four subband regions of one (d, l) tile: rows ky0 .. ky0 + cyn
+// and columns kx0 .. kx0 + cxn (periodic) into cf[s][row][col], s = 2 yb + xb;
+// subband 0 (LL) comes from `ll` (row stride lls).
+template <typename R>
+__device__ __forceinline__ void inv_stage(R* cf, const R* __restrict__ Ad, const R* __restrict__ ll,
+                                          int64_t lls, int nx, int hy, int hx, int ky0, int kx0, int cyn,
+                                          int cxn) {
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    if (lane < cxn) {
+        const int gx = (kx0 + lane) & (hx - 1);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            for (int yy = wy; yy < cyn; yy += 8) {
+                const int gy = (ky0 + yy) & (hy - 1);
+                const R* src = (s == 0) ? ll + (int64_t)gy * lls + gx
+                                        : Ad + (int64_t)((s >> 1) * hy + gy) * nx + (s & 1) * hx + gx;
+                cp_async(cf + (s * DC + yy) * SCF + lane, src);
             }
-            const int oy = k0y + r;
-            if (xlow) LLo[(int64_t)oy * lls + ox] = lo;
-            else Ad[(int64_t)oy * nx + ox] = lo;
-            Ad[(int64_t)(hy + oy) * nx + ox] = hi;
+    }
+    cp_async_commit();
+}
+
+// Synthesis along y: thread (x, b, mg) makes rows 2m, 2m + 1 for m = 4mg .. 4mg + 3
+// of column x of the x-lowpass (b = 0) or x-highpass (b = 1) half. Output row
+// 2m + p takes taps h[2k + p], g[2k + p] on coefficient rows m - k.
+template <typename R, int D>
+__device__ __forceinline__ void inv_cols(const R* __restrict__ cf, R* __restrict__ cl, int qy, int cxn) {
+    constexpr int H = D + 1;   // taps per parity
+    constexpr int NV = H + 3;
+    const int x = threadIdx.x & 31, b = (threadIdx.x >> 5) & 1, m0 = 4 * (threadIdx.x >> 6);
+    if (x >= cxn || m0 >= qy) return;
+    R a[NV], e[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        a[t] = cf[(b * DC + m0 + t) * SCF + x];
+        e[t] = cf[((2 + b) * DC + m0 + t) * SCF + x];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        R v0 = 0, v1 = 0;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const int t = u - k + H - 1;
+            v0 = fma(filt<R>(D, 0, 2 * k), a[t], v0);
+            v0 = fma(filt<R>(D, 1, 2 * k), e[t], v0);
+            v1 = fma(filt<R>(D, 0, 2 * k + 1), a[t], v1);
+            v1 = fma(filt<R>(D, 1, 2 * k + 1), e[t], v1);
+        }
+        if (m0 + u < qy) {
+            cl[(2 * (m0 + u)) * SCL + b * SCF + x] = v0;
+            cl[(2 * (m0 + u) + 1) * SCL + b * SCF + x] = v1;
         }
     }
 }
 
-// Loads the four subband tiles (with the periodic halo of the synthesis
-// filters) of one (d, l) and reconstructs the 2q x 2q output tile; thread
-// (lane, wy) accumulates output rows wy, wy + 8, ... (up to 4) at column lane.
-template <typename R>
-__device__ __forceinline__ void dwt_inv_tile(const R* __restrict__ Ad, const R* __restrict__ ll,
-                                             int64_t lls, int d, int nx, int my, int mx, int ty, int tx,
-                                             R (*cf)[DC][DC + 1], R (*cl)[2][DC + 1], R* acc) {
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int F = 2 * (d + 1);
-    const int hy = my >> 1, hx = mx >> 1;
-    const int qy = min(DQ, hy), qx = min(DQ, hx);
-    const int h2 = F / 2 - 1;
-    const int cyn = qy + h2, cxn = qx + h2;
-    const int ky0 = ty * qy - h2, kx0 = tx * qx - h2;
-    __syncthreads();   // previous use of cf / cl is finished
-    for (int q = 0; q < 4; ++q) {
-        const int yb = q >> 1, xb = q & 1;
-        for (int yy = wy; yy < cyn; yy += 8) {
-            const int gy = (ky0 + yy) & (hy - 1);
-            const R* row = (q == 0) ? ll + (int64_t)gy * lls : Ad + (int64_t)(yb * hy + gy) * nx + xb * hx;
-            for (int xx = lane; xx < cxn; xx += 32) cf[q][yy][xx] = row[(kx0 + xx) & (hx - 1)];
-        }
-    }
-    __syncthreads();
-    // columns: output row i (0..2qy), coefficient column xx, x-half b
-    for (int i = wy; i < 2 * qy; i += 8)
-        for (int xx = lane; xx < 2 * cxn; xx += 32) {
-            const int b = xx >= cxn, x = xx - b * cxn;
-            R v = 0;
-            for (int j = (i & 1); j < F; j += 2) {
-                const int kk = ((i - j) >> 1) + h2;
-                v = fma(filt<R>(d, 0, j), cf[b][kk][x], v);
-                v = fma(filt<R>(d, 1, j), cf[2 + b][kk][x], v);
-            }
-            cl[i][b][x] = v;
-        }
-    __syncthreads();
-    if (lane < 2 * qx) {
-        const int c = lane;
+// Synthesis along x, accumulated: thread (i, ng) adds output columns
+// 4ng .. 4ng + 3 of tile row i into acc.
+template <typename R, int D>
+__device__ __forceinline__ void inv_rows(const R* __restrict__ cl, R* acc, int qy, int qx) {
+    constexpr int H = D + 1;
+    constexpr int NV = H + 1;
+    const int i = threadIdx.x & 31, n0 = 2 * (threadIdx.x >> 5);
+    if (i >= 2 * qy || n0 >= qx) return;
+    R a[NV], e[NV];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {   // rows
-            const int i = wy + 8 * e;
-            if (i >= 2 * qy) break;
-            R v = 0;
-            for (int j = (c & 1); j < F; j += 2) {
-                const int kk = ((c - j) >> 1) + h2;
-                v = fma(filt<R>(d, 0, j), cl[i][0][kk], v);
-                v = fma(filt<R>(d, 1, j), cl[i][1][kk], v);
-            }
-            acc[e] += v;
-        }
+    for (int t = 0; t < NV; ++t) {
+        a[t] = cl[i * SCL + n0 + t];
+        e[t] = cl[i * SCL + SCF + n0 + t];
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        R v0 = 0, v1 = 0;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const int t = u - k + H - 1;
+            v0 = fma(filt<R>(D, 0, 2 * k), a[t], v0);
+            v0 = fma(filt<R>(D, 1, 2 * k), e[t], v0);
+            v1 = fma(filt<R>(D, 0, 2 * k + 1), a[t], v1);
+            v1 = fma(filt<R>(D, 1, 2 * k + 1), e[t], v1);
+        }
+        acc[2 * u] += v0;
+        acc[2 * u + 1] += v1;
+    }
+}
+
+// Writes the 2qy x 2qx tile held in acc (thread (i, ng): row i, columns
+// 4ng .. 4ng + 3) through the shared transpose buffer T with coalesced rows:
+// out[r * stride + c] = s * (T[r][c] + (add ? add[r * stride + c] : 0)).
+template <typename R>
+__device__ __forceinline__ void tile_store(R* T, const R* acc, R* __restrict__ out, const R* __restrict__ add,
+                                           int64_t stride, int qy, int qx, R s) {
+    constexpr int ST = 2 * DQ + 1;
+    const int i = threadIdx.x & 31, c0 = 4 * (threadIdx.x >> 5);
+    if (i < 2 * qy && c0 < 2 * qx)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) T[i * ST + c0 + u] = acc[u];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    if (lane < 2 * qx)
+        for (int r = wy; r < 2 * qy; r += 8) {
+            const int64_t o = (int64_t)r * stride + lane;
+            R v = T[r * ST + lane];
+            if (add) v += add[o];
+            out[o] = s * v;
+        }
 }
 
 // One synthesis level > 0 for every (d, l): reconstructs the my x mx block
-// (compact, stride mx, into `out`) from its LL (`ll`: A[1+d] at the coarsest
+// (compact, stride mx, into `out`) from its LL (`llbuf`: A[1+d] at the coarsest
 // level, else the coarser level's output, compact stride mx / 2) and A[1+d].
 template <typename R>
 __global__ void __launch_bounds__(256) k_dwt_inv_level(const R* __restrict__ A, const R* __restrict__ llbuf,
                                                       int ll_from_a, R* __restrict__ out, int L, int ny,
                                                       int nx, int my, int mx) {
-    __shared__ R cf[4][DC][DC + 1];
-    __shared__ R cl[2 * DQ][2][DC + 1];
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* cf = reinterpret_cast<R*>(smem_raw);
+    R* cl = cf + 2 * 4 * DC * SCF;
     const int d = blockIdx.y / L, l = blockIdx.y - d * L;
     const int hy = my >> 1, hx = mx >> 1;
     const int qy = min(DQ, hy), qx = min(DQ, hx);
@@ -185,49 +374,81 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level(const R* __restrict__ A, 
     const R* ll = ll_from_a ? Ad : llbuf + ((int64_t)d * L + l) * (int64_t)hy * hx;
     const int64_t lls = ll_from_a ? nx : hx;
     R acc[4] = {0, 0, 0, 0};
-    dwt_inv_tile<R>(Ad, ll, lls, d, nx, my, mx, ty, tx, cf, cl, acc);
-    R* o = out + ((int64_t)d * L + l) * (int64_t)my * mx;
-    if (lane < 2 * qx)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = wy + 8 * e;
-            if (i >= 2 * qy) break;
-            o[(int64_t)(2 * ty * qy + i) * mx + 2 * tx * qx + lane] = acc[e];
-        }
+#define HS_INV(DD)                                                                                   \
+    {                                                                                                \
+        constexpr int H = DD + 1;                                                                    \
+        inv_stage(cf, Ad, ll, lls, nx, hy, hx, ty * qy - (H - 1), tx * qx - (H - 1), qy + H - 1,     \
+                  qx + H - 1);                                                                       \
+        cp_async_wait<0>();                                                                          \
+        __syncthreads();                                                                             \
+        inv_cols<R, DD>(cf, cl, qy, qx + H - 1);                                                     \
+        __syncthreads();                                                                             \
+        inv_rows<R, DD>(cl, acc, qy, qx);                                                            \
+    }
+    HS_DWT_DISPATCH(d, HS_INV)
+#undef HS_INV
+    __syncthreads();
+    R* o = out + ((int64_t)d * L + l) * (int64_t)my * mx + (int64_t)(2 * ty * qy) * mx + 2 * tx * qx;
+    tile_store<R>(cl, acc, o, nullptr, mx, qy, qx, (R)1);
 }
 
-// Level-0 synthesis summed over the 9 bases: X[l] = (A[0][l] + sum_d W_d^T A[1+d][l]) / 3.
-// One CTA per (channel, output tile); the wavelets are accumulated in registers.
+template <typename R> struct InvCtx {
+    R* cf;
+    R* cl;
+    const R* A;
+    const R* llbuf;
+    int64_t N;
+    int L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a;
+};
+
+template <typename R, int D> __device__ __forceinline__ void inv_stage_d(const InvCtx<R>& c) {
+    constexpr int H = D + 1;
+    const R* Ad = c.A + ((int64_t)(1 + D) * c.L + c.l) * c.N;
+    const R* ll = c.ll_from_a ? Ad : c.llbuf + ((int64_t)D * c.L + c.l) * (int64_t)c.hy * c.hx;
+    inv_stage(c.cf + (D & 1) * 4 * DC * SCF, Ad, ll, c.ll_from_a ? c.nx : c.hx, c.nx, c.hy, c.hx,
+              c.ty * c.qy - (H - 1), c.tx * c.qx - (H - 1), c.qy + H - 1, c.qx + H - 1);
+}
+
+// Level-0 synthesis of all eight wavelets, the next wavelet's subbands staged
+// while the current one is filtered.
+template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCtx<R>& c, R* acc) {
+    if constexpr (D < NW) {
+        if constexpr (D + 1 < NW) {
+            inv_stage_d<R, D + 1>(c);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        inv_cols<R, D>(c.cf + (D & 1) * 4 * DC * SCF, c.cl, c.qy, c.qx + D);
+        __syncthreads();
+        inv_rows<R, D>(c.cl, acc, c.qy, c.qx);
+        inv_all<R, D + 1>(c, acc);
+    }
+}
+
+// Level-0 synthesis summed over the 9 bases: X[l] = (A[0][l] + sum_d W_d^T A[1+d][l]) / 3,
+// one CTA per (output tile, channel).
 template <typename R>
-__global__ void __launch_bounds__(256) k_dwt_inv_level0_sum(const R* __restrict__ A, const R* __restrict__ llbuf,
-                                                           int ll_from_a, R* __restrict__ X, int L, int ny,
-                                                           int nx, R s) {
-    __shared__ R cf[4][DC][DC + 1];
-    __shared__ R cl[2 * DQ][2][DC + 1];
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_psi_adj_l0(const R* __restrict__ A, const R* __restrict__ llbuf,
+                                                   int ll_from_a, R* __restrict__ X, int L, int ny, int nx,
+                                                   R s) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* cf = reinterpret_cast<R*>(smem_raw);
+    R* cl = cf + 2 * 4 * DC * SCF;
     const int l = blockIdx.y;
     const int hy = ny >> 1, hx = nx >> 1;
     const int qy = min(DQ, hy), qx = min(DQ, hx);
     const int ntx = hx / qx;
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int64_t N = (int64_t)ny * nx;
+    InvCtx<R> c{cf, cl, A, llbuf, N, L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a};
+    inv_stage_d<R, 0>(c);
     R acc[4] = {0, 0, 0, 0};
-    for (int d = 0; d < NW; ++d) {
-        const R* Ad = A + ((int64_t)(1 + d) * L + l) * N;
-        const R* ll = ll_from_a ? Ad : llbuf + ((int64_t)d * L + l) * (int64_t)hy * hx;
-        const int64_t lls = ll_from_a ? nx : hx;
-        dwt_inv_tile<R>(Ad, ll, lls, d, nx, ny, nx, ty, tx, cf, cl, acc);
-    }
-    const R* A0 = A + (int64_t)l * N;
-    R* o = X + (int64_t)l * N;
-    if (lane < 2 * qx)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = wy + 8 * e;
-            if (i >= 2 * qy) break;
-            const int64_t idx = (int64_t)(2 * ty * qy + i) * nx + 2 * tx * qx + lane;
-            o[idx] = s * (acc[e] + A0[idx]);
-        }
+    inv_all<R, 0>(c, acc);
+    __syncthreads();
+    const int64_t t0 = (int64_t)(2 * ty * qy) * nx + 2 * tx * qx;
+    tile_store<R>(cl, acc, X + l * N + t0, A + l * N + t0, nx, qy, qx, s);
 }
 
 static hs_status upload_filters() {
@@ -252,9 +473,23 @@ static hs_status upload_filters() {
     return HS_OK;
 }
 
-hs_status dwt_init() { return upload_filters(); }
+template <typename K> static hs_status smem_attr(K k, int bytes) {
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return HS_OK;
+}
 
-static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+hs_status dwt_init() {
+    HS_TRY(upload_filters());
+    HS_TRY(smem_attr(k_psi_fwd_l0<float>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_fwd_l0<double>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_fwd_level<float>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_fwd_level<double>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_inv_level<float>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_inv_level<double>, INV_SMEM * 8));
+    HS_TRY(smem_attr(k_psi_adj_l0<float>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_adj_l0<double>, INV_SMEM * 8));
+    return HS_OK;
+}
 
 static inline unsigned ntiles(int my, int mx) {
     const int hy = my >> 1, hx = mx >> 1;
@@ -264,17 +499,16 @@ static inline unsigned ntiles(int my, int mx) {
 
 template <typename R> static hs_status analysis_t(Plan* p, const R* X, R* A, cudaStream_t s) {
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
-    const int64_t N = p->N();
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
-    const R third = (R)(1.0 / 3.0);
-    const unsigned gs = nblk(L * N, 256);
-    k_scale_copy<R><<<gs > 4096 ? 4096 : gs, 256, 0, s>>>(X, A, L * N, third);
+    const int top = p->levels - 1;
+    k_psi_fwd_l0<R><<<dim3(ntiles(ny, nx), L), 256, FWD_SMEM * sizeof(R), s>>>(X, A, buf[0], L, ny, nx, top == 0,
+                                                                              (R)(1.0 / 3.0));
     HS_CHECK_LAUNCH();
-    for (int lev = 0; lev < p->levels; ++lev) {
+    for (int lev = 1; lev <= top; ++lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
-        k_dwt_fwd_level<R><<<g, 256, 0, s>>>(X, lev ? buf[(lev - 1) & 1] : nullptr, A, buf[lev & 1], L, ny,
-                                             nx, my, mx, lev == 0, lev == p->levels - 1, third);
+        k_dwt_fwd_level<R><<<g, 256, FWD_SMEM * sizeof(R), s>>>(buf[(lev - 1) & 1], A, buf[lev & 1], L, ny, nx,
+                                                                my, mx, lev == top);
         HS_CHECK_LAUNCH();
     }
     return HS_OK;
@@ -287,13 +521,12 @@ template <typename R> static hs_status synthesis_t(Plan* p, const R* A, R* X, cu
     for (int lev = top; lev >= 1; --lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
-        k_dwt_inv_level<R><<<g, 256, 0, s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1], lev == top,
-                                             buf[lev & 1], L, ny, nx, my, mx);
+        k_dwt_inv_level<R><<<g, 256, INV_SMEM * sizeof(R), s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1],
+                                                                lev == top, buf[lev & 1], L, ny, nx, my, mx);
         HS_CHECK_LAUNCH();
     }
-    dim3 g0(ntiles(ny, nx), L);
-    k_dwt_inv_level0_sum<R><<<g0, 256, 0, s>>>(A, top == 0 ? nullptr : buf[1], top == 0, X, L, ny, nx,
-                                               (R)(1.0 / 3.0));
+    k_psi_adj_l0<R><<<dim3(ntiles(ny, nx), L), 256, INV_SMEM * sizeof(R), s>>>(
+        A, top == 0 ? nullptr : buf[1], top == 0, X, L, ny, nx, (R)(1.0 / 3.0));
     HS_CHECK_LAUNCH();
     return HS_OK;
 }

@@ -69,18 +69,19 @@ __device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partn
     constexpr int LG = (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     T *a = A, *b = B, *v = V, *w = W;
+    const T skipT = (T)skip;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        double nrm = 0.0, off = 0.0;
+        T nrmT = 0, offT = 0;   // per-thread partial sums in the working precision
         for (int k = tid; k < N * N; k += nt) {
             const int i = k >> LG, j = k & (N - 1);
-            const double x = (double)a[i * LDJ + j];
-            nrm += x * x;
-            if (i != j) off += x * x;
+            const T x = a[i * LDJ + j];
+            nrmT = fma(x, x, nrmT);
+            if (i != j) offT = fma(x, x, offT);
         }
-        nrm = eig_bsum(nrm, red);
-        off = eig_bsum(off, red);
+        const double nrm = eig_bsum((double)nrmT, red);
+        const double off = eig_bsum((double)offT, red);
         if (!(off > off_rel * off_rel * nrm)) break;
-        const double flo = floor_rel * sqrt(nrm);
+        const T flo = (T)(floor_rel * sqrt(nrm));
         if (tid == 0) *flag = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
@@ -90,8 +91,8 @@ __device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partn
                 const int p = i < pi ? i : pi, q = i < pi ? pi : i;
                 const T apq = a[p * LDJ + q], app = a[p * LDJ + p], aqq = a[q * LDJ + q];
                 T c = 1, s = 0;
-                const double ab = fabs((double)apq);
-                if (ab > flo && ab > 1e-300 && ab > skip * sqrt(fabs((double)app * (double)aqq))) {
+                const T ab = fabs(apq);
+                if (ab > flo && ab > T(0) && ab > skipT * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
                     const T tau = (aqq - app) / (T(2) * apq);
                     const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
                     c = T(1) / sqrt(T(1) + t * t);

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libhypersara.so")
 HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_NOMEM, HS_ERR_TIMEOUT, HS_ERR_STATE = 0, -1, -2, -3, -4, -5
 HS_F32, HS_F64 = 0, 1
 HS_PLAN_COMPENSATED = 1
+STAGES = {"fft_fwd": 0, "degrid": 1, "grid": 2, "fft_adj": 3, "psi_fwd": 4, "psi_adj": 5}
 
 _lib = None
 
@@ -74,6 +75,7 @@ _SIGS = {
     "hs_pd_iterations": ([_P, C.POINTER(C.c_int64)], C.c_int),
     "hs_pd_graph_kernels": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hs_pd_nuclear_info": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int), _P], C.c_int),
+    "hs_time_stage": ([_P, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_float), _P], C.c_int),
     "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
 }
@@ -247,6 +249,13 @@ class Plan:
         r = C.c_double()
         _check("hs_norm_l21", load().hs_norm_l21(self.h, _ptr(A), _ptr(w_rows), C.byref(r), _stream()))
         return r.value
+
+    def time_stage(self, stage: str, inp=None, out=None, reps: int = 20) -> float:
+        """Mean duration (ms) of one stage launched alone (hs_time_stage)."""
+        ms = C.c_float()
+        _check("hs_time_stage", load().hs_time_stage(self.h, STAGES[stage], _ptr(inp), _ptr(out), int(reps),
+                                                     C.byref(ms), _stream()))
+        return ms.value
 
     def op_norm2(self, iters: int = 500, tol: float = 1e-10, seed: int = 0) -> float:
         r = C.c_double()

@@ -242,3 +242,22 @@ def test_norm_l21(prec):
         A = A.astype(np.float32).astype(np.float64)
     got = plan.norm_l21(dev(A, prec))
     assert got == pytest.approx(np.sum(prox.row_norms(A)), rel=1e-12 if prec == "f64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_time_stage_runs_every_stage(prec):
+    c = _case("ragged64", prec)
+    plan = make_plan(c, prec)
+    X = dev(c["X"], prec)
+    Y = dev(c["Y"], prec, True)
+    Xo = plan.cube()
+    A = plan.cube(9)
+    io = {"fft_fwd": (X, None), "degrid": (None, Y), "grid": (Y, None), "fft_adj": (None, Xo),
+          "psi_fwd": (X, A), "psi_adj": (A, Xo)}
+    for name, (i, o) in io.items():
+        assert plan.time_stage(name, i, o, reps=2) > 0.0
+    # the stages compose to the operators: grid then adjoint FFT is phi_adj
+    plan.time_stage("grid", Y, None, reps=1)
+    plan.time_stage("fft_adj", None, Xo, reps=1)
+    ref = host(plan.phi_adj(Y))
+    assert rel(host(Xo), ref) <= (1e-14 if prec == "f64" else 1e-6)
