@@ -199,6 +199,30 @@ HS_API hs_status hs_proj_l2ball(hs_plan_t plan, const void* Z, const void* Yd, c
                          int dual, void* out, double* rho_out, void* stream);
 
 /*
+ * hs_proj_l2ball_static - the projection of hs_proj_l2ball without a plan and
+ * without any device allocation (the paper has no counterpart: it exists for
+ * callers that hold only device pointers and must not allocate). Its scratch
+ * is a fixed device array of HS_L2BALL_STATIC_DOUBLES doubles inside the
+ * library (partial sums and per-channel scales); nothing in it needs to start
+ * at zero.
+ *   L:           channels, 1 <= L <= HS_L2BALL_STATIC_MAX_L (else HS_ERR_ARG,
+ *                detected on the host before any launch);
+ *   vis_offsets: DEVICE L + 1 int64, channel l owns [vis_offsets[l], vis_offsets[l+1]);
+ *   Z, Yd, out:  DEVICE complex of `prec`, indexed by those offsets; out may equal Z;
+ *   eps, rho_out, dual: as in hs_proj_l2ball (rho_out may be NULL).
+ * The first call on a device (that device current) looks up the scratch
+ * address with cudaGetSymbolAddress, which may load the library's device
+ * code, and caches it; make that call before any stream capture. The scratch
+ * is shared by every call on the device: calls whose executions overlap (two
+ * streams or host threads) race and give wrong results.
+ */
+#define HS_L2BALL_STATIC_DOUBLES 65536
+#define HS_L2BALL_STATIC_MAX_L 16384
+HS_API hs_status hs_proj_l2ball_static(int L, const int64_t* vis_offsets, const void* Z, const void* Yd,
+                                const double* eps, hs_prec prec, int dual, void* out, double* rho_out,
+                                void* stream);
+
+/*
  * hs_norm_l21 - sum_n w_n ||a_n||_2 over the rows of a coefficient cube
  * (the weighted l2,1 norm of Sec. 2.3). w_rows as in hs_prox_l21. The result is
  * written to *out_host after the stream has been synchronised.

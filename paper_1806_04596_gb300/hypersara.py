@@ -64,6 +64,7 @@ _SIGS = {
     "hs_prox_l21": ([_P, _P, _P, C.c_double, C.c_int, _P, _P], C.c_int),
     "hs_prox_nuclear": ([_P, _P, _P, C.c_double, C.c_int, _P, _P, _P], C.c_int),
     "hs_proj_l2ball": ([_P, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
+    "hs_proj_l2ball_static": ([C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P], C.c_int),
     "hs_norm_l21": ([_P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
     "hs_op_norm2": ([_P, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double), _P], C.c_int),
     "hs_pd_state_create": ([_P, _P, _P, C.POINTER(PDParams), C.POINTER(C.c_void_p), _P], C.c_int),
@@ -108,6 +109,11 @@ def _check(fn: str, st: int):
 
 def version() -> str:
     return load().hs_version().decode()
+
+
+def last_error() -> str:
+    """The calling thread's last error message (hs_last_error)."""
+    return load().hs_last_error().decode(errors="replace")
 
 
 def daubechies_lowpass(p: int) -> np.ndarray:
@@ -356,6 +362,26 @@ def prox_nuclear(plan: Plan, X, thr, w_sv=None, dual=False, out=None):
 
 def proj_l2ball(plan: Plan, Z, Yd, eps, dual=False, out=None):
     return plan.proj_l2ball(Z, Yd, eps, dual, out)
+
+
+L2BALL_STATIC_MAX_L = 16384   # HS_L2BALL_STATIC_MAX_L
+
+
+def proj_l2ball_static(offsets, Z, Yd, eps, dual=False, out=None, prec: str = "f32"):
+    """hs_proj_l2ball_static: plan-free projection whose scratch is a fixed
+    device array inside the library (no device allocation in the call).
+    offsets: int64 CUDA tensor (L + 1,); eps: FP64 CUDA tensor (L,).
+    Returns (out, rho)."""
+    torch = _torch()
+    if prec not in ("f32", "f64"):
+        raise ValueError("prec must be 'f32' or 'f64'")
+    L = int(offsets.numel()) - 1
+    out = torch.empty_like(Z) if out is None else out
+    rho = torch.empty(max(L, 0), dtype=torch.float64, device="cuda")
+    _check("hs_proj_l2ball_static",
+           load().hs_proj_l2ball_static(L, _ptr(offsets), _ptr(Z), _ptr(Yd), _ptr(eps), HS_F32 if prec == "f32" else HS_F64, int(dual),
+                                        _ptr(out), _ptr(rho), _stream()))
+    return out, rho
 
 
 def pd_step(state: PDState):

@@ -76,3 +76,14 @@ def test_host_argument_errors_without_gpu(lib):
     assert L.hs_phi_fwd(None, None, None, None) == lib.HS_ERR_ARG
     assert L.hs_pd_step(None, None) == lib.HS_ERR_ARG
     assert L.hs_plan_destroy(None) == lib.HS_OK
+
+
+def test_static_l2ball_rejects_channel_counts_on_the_host(lib):
+    """hs_proj_l2ball_static checks L against its fixed scratch before any CUDA call."""
+    L = lib.load()
+    for bad in (0, -1, lib.L2BALL_STATIC_MAX_L + 1):
+        st = L.hs_proj_l2ball_static(bad, None, None, None, None, 0, 0, None, None, None)
+        assert st == -1, (bad, st)
+        assert "outside" in lib.last_error()
+    st = L.hs_proj_l2ball_static(4, None, None, None, None, 0, 0, None, None, None)
+    assert st == -1 and "null" in lib.last_error()
