@@ -66,9 +66,10 @@ typedef enum {
 typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
 
 /* plan flags */
-/* Gridding with per-warp private tiles summed in a fixed order (bitwise
- * reproducible), Kahan-compensated in FP32 plans. Without it gridding uses
- * shared-memory atomic additions: faster, equal to rounding, order not fixed. */
+/* Gridding adds one window per warp at a time with Kahan-compensated sums
+ * (FP32 plans). Without it each warp adds 4 non-overlapping windows at once,
+ * uncompensated: faster. Both keep per-warp private tiles summed in a fixed
+ * order, so both are bitwise reproducible. */
 #define HS_PLAN_COMPENSATED 1u
 
 typedef struct hs_plan* hs_plan_t;
@@ -118,7 +119,7 @@ HS_API hs_status hs_plan_destroy(hs_plan_t plan);
 typedef struct {
     int nx, ny, L, Kx, Ky, levels, prec, flags;
     int64_t total_vis;
-    int64_t grid_tile_entries;    /* visibility-tile pairs in the gridding lists */
+    int64_t grid_tile_entries;    /* gridding list slots: visibility-tile pairs plus group padding */
     int tile_x, tile_y;           /* gridding tile size in grid cells */
     int kb_terms;                 /* coefficients per kernel polynomial piece */
     double kb_beta;

@@ -41,7 +41,6 @@ constexpr int KB_TERMS_F64 = 14;     // ... FP64
 constexpr int GRID_TILE = 32;        // gridding tile side (cells)
 constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumulators)
 constexpr int GRID_CAP = 512;        // most list entries one gridding CTA processes
-constexpr int GRID_AWARPS = 8;       // warps per CTA of the shared-atomic gridding kernel
 constexpr int DEGRID_CHUNK = 256;    // visibilities per degridding CTA
 constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
 
@@ -79,7 +78,8 @@ struct Plan {
     void* u_sorted = nullptr;          // U in sorted order (real) or null
     int64_t n_ent = 0;
     int64_t* tile_off = nullptr;       // L * ntiles + 1
-    int* tile_ent = nullptr;           // sorted visibility index per (channel, tile) entry
+    int* tile_ent = nullptr;           // per (channel, tile): groups of 4 sorted visibility indices
+                                       // with non-overlapping windows, -1 = padding
     void* grid_items = nullptr;        // gridding work items {tix, e0, e1, slot}
     int64_t n_items = 0;
     void* grid_merges = nullptr;       // split tiles {tix, slot0, nslot}

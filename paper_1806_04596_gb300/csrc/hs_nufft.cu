@@ -13,12 +13,14 @@
 // neighbouring lanes touch neighbouring grid cells.
 //
 // Gridding: one CTA per (channel, 32 x 32 output tile) consumes the tile's list
-// of visibilities whose window overlaps it (built by the plan). Each warp adds
-// whole windows (two rows of 32 lanes) into its own private copy of the tile
-// in shared memory, so no atomics are needed anywhere; the copies are summed
-// in a fixed order and every output cell is written exactly once, so the
-// result is deterministic and the grid needs no zeroing pass. With
-// HS_PLAN_COMPENSATED the FP32 accumulation is Kahan-compensated.
+// of visibilities whose window overlaps it (built by the plan) and writes every
+// output cell of the tile exactly once, so the grid needs no zeroing pass and
+// no global atomics. Every warp adds windows into its own private copy of the
+// tile in shared memory and the copies are combined in a fixed order, so the
+// result is deterministic. Default kernel: the plan groups each list into 4
+// mutually non-overlapping windows, which one warp adds at once (8 lanes per
+// window). HS_PLAN_COMPENSATED kernel: one window per warp at a time, with
+// Kahan-compensated FP32 sums.
 #include "hs_device.cuh"
 #include "hs_internal.h"
 
@@ -217,8 +219,9 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
         const int e = base + lane;
         const int nb = min(32, it.e1 - base);
         R fx = 0, fy = 0;
-        if (e < it.e1) {
-            const int64_t i = a.tile_ent[e];
+        const int64_t i = e < it.e1 ? a.tile_ent[e] : -1;   // -1: padding of the plan's groups
+        s_k0[w][lane] = make_int2(-1, -1);
+        if (i >= 0) {
             int cxv, cyv;
             VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
             const int k0x = (cxv - 3) & (Kx - 1);
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
         __syncwarp();
         for (int k = 0; k < nb; ++k) {
             const int2 b0 = s_k0[w][k];
+            if (b0.x < 0) continue;
             const int gx = ((b0.x + cc) & (Kx - 1)) - tx0;
             if (gx >= 0 && gx < TX) {
                 const CT vv = s_val[w][k];
@@ -316,28 +320,25 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
     }
 }
 
-// Default gridding kernel: one shared tile per CTA (row stride GRID_TILE + 8
-// complex values) and shared-memory atomic additions. The additions of a
-// window do not wait for one another, so eight warps stream windows without
-// the read-modify-write chain of the private-tile kernel above. A window is
-// added by a whole warp (lanes = 8 columns x 4 rows, two row passes), so the
-// 64 cells of one atomic instruction are distinct. Per batch of 32 entries the
-// column products phi_u(c) v and row weights phi_v(r) are staged in shared
-// memory. The summation order inside a tile is not fixed (results agree to
-// rounding).
-template <typename R> struct GridAW { static constexpr int value = sizeof(R) == 8 ? 4 : GRID_AWARPS; };
+// Default gridding kernel. The plan orders every tile list in groups of 4
+// entries whose windows do not overlap (padding -1). Each of the GRID_PW warps
+// of a CTA owns a private copy of the tile in shared memory and adds one group
+// per pass: 8 lanes per window (lane j: column j, all 8 rows; the row weights
+// are exchanged by shuffles inside the 8 lanes), so the 32 lanes of a pass
+// update 4 x 8 distinct cells with plain loads and stores and no atomics. A
+// warp fetches the entries of 4 groups at once (one lane per entry) so their
+// loads are in flight together. The copies are summed in a fixed order: the
+// result is deterministic.
+constexpr int GRID_PW = 4;          // warps (private tiles) per CTA
+constexpr int GRID_LDT = GRID_TILE + 1;
 
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(GridAW<R>::value * 32) k_grid_atomic(NufftK<R> a,
-                                                                     const GridItem* __restrict__ items,
-                                                                     Cx<R>* __restrict__ partial) {
+__global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const GridItem* __restrict__ items,
+                                                              Cx<R>* __restrict__ partial) {
     typedef Cx<R> CT;
-    constexpr int LDT = GRID_TILE + 8;
-    constexpr int AW = GridAW<R>::value;   // warps (static smem stays < 48 KB)
-    __shared__ __align__(16) R tile[GRID_TILE * LDT * 2];
-    __shared__ int2 s_k0[AW][32];          // window start cells
-    __shared__ CT s_pv[AW][32][8];         // phi_u(c) * v
-    __shared__ R s_pw[AW][32][8];          // phi_v(r)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT* priv = reinterpret_cast<CT*>(smem_raw);   // [GRID_PW][GRID_TILE][GRID_LDT]
+    constexpr int TCELLS = GRID_TILE * GRID_LDT;
     const GridItem it = items[blockIdx.x];
     const int TX = a.g.tx, TY = a.g.ty;
     const int ntiles = a.g.ntx * a.g.nty;
@@ -346,67 +347,76 @@ __global__ void __launch_bounds__(GridAW<R>::value * 32) k_grid_atomic(NufftK<R>
     const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
     const int ty0 = tyi * TY, tx0 = txi * TX;
     const int Kx = a.g.Kx, Ky = a.g.Ky;
-    for (int k = threadIdx.x; k < GRID_TILE * LDT * 2; k += blockDim.x) tile[k] = (R)0;
+    for (int k = threadIdx.x; k < GRID_PW * TCELLS; k += blockDim.x) priv[k] = cx<R>(0, 0);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = lane >> 4, sub = lane & 15;
+    const int j = lane & 7, grp = lane >> 3;
+    const unsigned gmask = 0xffu << (8 * grp);
+    CT* mine = priv + w * TCELLS;
     R c[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - (sub & 7)) * NC + k];
-    const int cc = lane & 7, r0 = lane >> 3;
-    for (int base = it.e0 + 32 * w; base < it.e1; base += 32 * AW) {
-        const int e = base + lane;
-        const int nb = min(32, it.e1 - base);
+    for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - j) * NC + k];
+    const int ng = (it.e1 - it.e0) >> 2;
+    for (int g0 = 4 * w; g0 < ng; g0 += 4 * GRID_PW) {
+        const int nbg = min(4, ng - g0);
+        // lane 4p + s fetches slot s of group g0 + p
+        int k0x = -1, k0y = 0;
         R fx = 0, fy = 0;
         CT val = cx<R>(0, 0);
-        if (e < it.e1) {
-            const int64_t i = a.tile_ent[e];
-            int cxv, cyv;
-            VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
-            const int k0x = (cxv - 3) & (Kx - 1);
-            const int k0y = (cyv - 3) & (Ky - 1);
-            if (MODE == GIN_CALLER) {
-                val = a.in[a.perm[i]];
-            } else if (MODE == GIN_SORTED) {
-                val = a.in[i];
-            } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
-                val = cscale(a.d[i], a.scale[l]);
-                if (a.u) val = cscale(val, sqrt(a.u[i]));
-                if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
+        if (lane < 4 * nbg) {
+            const int64_t i = a.tile_ent[it.e0 + 4 * g0 + lane];
+            if (i >= 0) {
+                int cxv, cyv;
+                VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+                k0x = (cxv - 3) & (Kx - 1);
+                k0y = (cyv - 3) & (Ky - 1);
+                if (MODE == GIN_CALLER) {
+                    val = a.in[a.perm[i]];
+                } else if (MODE == GIN_SORTED) {
+                    val = a.in[i];
+                } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
+                    val = cscale(a.d[i], a.scale[l]);
+                    if (a.u) val = cscale(val, sqrt(a.u[i]));
+                    if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
+                }
+                if (a.w) val = cscale(val, a.w[i]);
             }
-            if (a.w) val = cscale(val, a.w[i]);
-            s_k0[w][lane] = make_int2(k0x, k0y);
         }
-        for (int k = 0; k < nb; k += 2) {
-            const int src = k + half;
-            const R fxs = __shfl_sync(0xffffffffu, fx, src);
-            const R fys = __shfl_sync(0xffffffffu, fy, src);
-            const R vxs = __shfl_sync(0xffffffffu, val.x, src);
-            const R vys = __shfl_sync(0xffffffffu, val.y, src);
-            const R phi = horner<R, NC>(c, (R)2 * (sub < 8 ? fxs : fys) - (R)1);
-            if (sub < 8) s_pv[w][src][sub] = cx<R>(phi * vxs, phi * vys);
-            else s_pw[w][src][sub - 8] = phi;
-        }
-        __syncwarp();
-#pragma unroll 2
-        for (int k = 0; k < nb; ++k) {
-            const int2 b0 = s_k0[w][k];
-            const int gx = ((b0.x + cc) & (Kx - 1)) - tx0;
-            if (gx >= 0 && gx < TX) {
-                const CT pv = s_pv[w][k][cc];
+        for (int p = 0; p < nbg; ++p) {
+            const int src = 4 * p + grp;
+            const int sx = __shfl_sync(0xffffffffu, k0x, src);
+            const int sy = __shfl_sync(0xffffffffu, k0y, src);
+            const R sfx = __shfl_sync(0xffffffffu, fx, src);
+            const R sfy = __shfl_sync(0xffffffffu, fy, src);
+            const R vr = __shfl_sync(0xffffffffu, val.x, src);
+            const R vi = __shfl_sync(0xffffffffu, val.y, src);
+            if (sx < 0) continue;   // padding; uniform over the 8 lanes of a window
+            const R phx = horner<R, NC>(c, (R)2 * sfx - (R)1);   // phi_u of column j
+            const R phy = horner<R, NC>(c, (R)2 * sfy - (R)1);   // phi_v of row j
+            const int gx = ((sx + j) & (Kx - 1)) - tx0;
+            const bool colok = (unsigned)gx < (unsigned)TX;
+            const R pr = phx * vr, pi = phx * vi;
+            // the 8 rows of a window are distinct cells: load all, add, store all
+            CT cur[8];
+            int off[8];
+            bool ok[8];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int rr = r0 + 4 * q;
-                    const int gy = ((b0.y + rr) & (Ky - 1)) - ty0;
-                    if (gy < 0 || gy >= TY) continue;
-                    const R pw = s_pw[w][k][rr];
-                    R* cell = tile + 2 * (gy * LDT + gx);
-                    atomicAdd(cell, pw * pv.x);
-                    atomicAdd(cell + 1, pw * pv.y);
+            for (int r = 0; r < 8; ++r) {
+                const int gy = ((sy + r) & (Ky - 1)) - ty0;
+                ok[r] = colok && (unsigned)gy < (unsigned)TY;
+                off[r] = gy * GRID_LDT + gx;
+                if (ok[r]) cur[r] = mine[off[r]];
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const R pw = __shfl_sync(gmask, phy, r, 8);
+                if (ok[r]) {
+                    cur[r].x = fma(pw, pr, cur[r].x);
+                    cur[r].y = fma(pw, pi, cur[r].y);
+                    mine[off[r]] = cur[r];
                 }
             }
         }
-        __syncwarp();
     }
     __syncthreads();
     CT* Gout;
@@ -420,8 +430,12 @@ __global__ void __launch_bounds__(GridAW<R>::value * 32) k_grid_atomic(NufftK<R>
     }
     for (int k = threadIdx.x; k < GRID_TILE * GRID_TILE; k += blockDim.x) {
         const int gy = k >> 5, gx = k & (GRID_TILE - 1);
-        if (gy < TY && gx < TX)
-            Gout[(int64_t)gy * gstride + gx] = cx<R>(tile[2 * (gy * LDT + gx)], tile[2 * (gy * LDT + gx) + 1]);
+        if (gy < TY && gx < TX) {
+            CT s = priv[gy * GRID_LDT + gx];
+#pragma unroll
+            for (int ww = 1; ww < GRID_PW; ++ww) s = cadd(s, priv[ww * TCELLS + gy * GRID_LDT + gx]);
+            Gout[(int64_t)gy * gstride + gx] = s;
+        }
     }
 }
 
@@ -502,7 +516,8 @@ static hs_status grid_launch(Plan* p, NufftK<R>& k, cudaStream_t s) {
         k_grid<R, NC, MODE, KAHAN><<<(unsigned)p->n_items, GRID_WARPS * 32, smem, s>>>(
             k, (const GridItem*)p->grid_items, (Cx<R>*)p->grid_partial);
     else
-        k_grid_atomic<R, NC, MODE><<<(unsigned)p->n_items, GridAW<R>::value * 32, 0, s>>>(
+        k_grid_groups<R, NC, MODE><<<(unsigned)p->n_items, GRID_PW * 32,
+                                     (size_t)GRID_PW * GRID_TILE * GRID_LDT * sizeof(Cx<R>), s>>>(
             k, (const GridItem*)p->grid_items, (Cx<R>*)p->grid_partial);
     HS_CHECK_LAUNCH();
     if (p->n_merges > 0) {
@@ -519,6 +534,9 @@ template <typename R, int NC, int MODE, bool KAHAN> static hs_status grid_attr()
     static_assert(sizeof(GridItem) == 16 && sizeof(GridMerge) == 12, "plan-side layout");
     HS_CHECK_CUDA(cudaFuncSetAttribute(k_grid<R, NC, MODE, KAHAN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (!KAHAN)
+        HS_CHECK_CUDA(cudaFuncSetAttribute(k_grid_groups<R, NC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(GRID_PW * GRID_TILE * GRID_LDT * sizeof(Cx<R>))));
     return HS_OK;
 }
 

@@ -211,8 +211,8 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
                 for (int xx = 0; xx < a; ++xx) ++toff[1 + (size_t)l * nt + tys[yy] * g.ntx + txs[xx]];
         }
     for (size_t k = 1; k < toff.size(); ++k) toff[k] += toff[k - 1];
-    p->n_ent = toff.back();
-    std::vector<int> ent((size_t)p->n_ent);
+    if (toff.back() >= ((int64_t)1 << 30)) return fail(HS_ERR_ARG, "too many gridding list entries");
+    std::vector<int> ent((size_t)toff.back());
     {
         std::vector<int64_t> fill(toff.begin(), toff.end() - 1);
         for (int l = 0; l < L; ++l)
@@ -224,23 +224,85 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
                         ent[fill[(size_t)l * nt + tys[yy] * g.ntx + txs[xx]]++] = (int)r;
             }
     }
-    HS_TRY(upload(p, (void**)&p->tile_off, toff));
-    HS_TRY(upload(p, (void**)&p->tile_ent, ent));
+    // Regroup every list into groups of 4 entries whose windows do not overlap
+    // (circular distance >= 8 cells in x or y), padding with -1, so that the
+    // gridding kernel can add the 4 windows of a group at once without atomics.
+    // Greedy, in list order: an entry joins the first open group it fits; at
+    // most GROUP_OPEN groups are open, the oldest is closed (padded) to make room.
+    std::vector<int64_t> goff((size_t)L * nt + 1, 0);
+    std::vector<int> gent;
+    gent.reserve((size_t)(toff.back() + toff.back() / 4 + 64));
+    {
+        constexpr int GROUP_OPEN = 8;
+        struct Group {
+            int m;
+            int e[4], x[4], y[4];
+        };
+        auto circ = [](int d, int K) {
+            d &= K - 1;
+            return d < K - d ? d : K - d;
+        };
+        std::vector<Group> open;
+        auto emit = [&](const Group& g) {
+            for (int k = 0; k < 4; ++k) gent.push_back(k < g.m ? g.e[k] : -1);
+        };
+        for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
+            open.clear();
+            for (int64_t q = toff[tix]; q < toff[tix + 1]; ++q) {
+                const int r = ent[q];
+                const int64_t i = perm[r];
+                const int x = (cellx[i] - 3) & (Kx - 1), y = (celly[i] - 3) & (Ky - 1);
+                bool placed = false;
+                for (size_t gi = 0; gi < open.size() && !placed; ++gi) {
+                    Group& g = open[gi];
+                    bool fits = true;
+                    for (int k = 0; k < g.m && fits; ++k)
+                        fits = circ(x - g.x[k], Kx) >= 8 || circ(y - g.y[k], Ky) >= 8;
+                    if (!fits) continue;
+                    g.e[g.m] = r;
+                    g.x[g.m] = x;
+                    g.y[g.m] = y;
+                    if (++g.m == 4) {
+                        emit(g);
+                        open.erase(open.begin() + gi);
+                    }
+                    placed = true;
+                }
+                if (placed) continue;
+                if ((int)open.size() == GROUP_OPEN) {
+                    emit(open.front());
+                    open.erase(open.begin());
+                }
+                Group g{};
+                g.m = 1;
+                g.e[0] = r;
+                g.x[0] = x;
+                g.y[0] = y;
+                open.push_back(g);
+            }
+            for (const Group& g : open) emit(g);
+            goff[tix + 1] = (int64_t)gent.size();
+        }
+    }
+    p->n_ent = goff.back();
     if (p->n_ent >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "too many gridding list entries");
-    // work items: lists longer than GRID_CAP are split; split tiles are merged
+    HS_TRY(upload(p, (void**)&p->tile_off, goff));
+    HS_TRY(upload(p, (void**)&p->tile_ent, gent));
+    // work items: lists longer than GRID_CAP entries are split at group
+    // boundaries; split tiles are merged
     {
         std::vector<int> items, merges;
         int slots = 0;
         for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
-            const int64_t a = toff[tix], b = toff[tix + 1];
-            const int64_t n = b - a;
-            const int parts = n <= GRID_CAP ? 1 : (int)((n + GRID_CAP - 1) / GRID_CAP);
+            const int64_t a = goff[tix], b = goff[tix + 1];
+            const int64_t ng = (b - a) / 4;
+            const int parts = ng * 4 <= GRID_CAP ? 1 : (int)((ng * 4 + GRID_CAP - 1) / GRID_CAP);
             if (parts == 1) {
                 items.insert(items.end(), {(int)tix, (int)a, (int)b, -1});
             } else {
                 merges.insert(merges.end(), {(int)tix, slots, parts});
                 for (int k = 0; k < parts; ++k) {
-                    const int64_t e0 = a + n * k / parts, e1 = a + n * (k + 1) / parts;
+                    const int64_t e0 = a + 4 * (ng * k / parts), e1 = a + 4 * (ng * (k + 1) / parts);
                     items.insert(items.end(), {(int)tix, (int)e0, (int)e1, slots + k});
                 }
                 slots += parts;
