@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
     for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - j) * NC + k];
     const int Kx = a.g.Kx, Ky = a.g.Ky;
     const CT* G = a.grid + (int64_t)l * Ky * Kx;
-    double sq = 0.0;
+    R sq = 0;   // this thread's share of ||d||^2 (few terms; FP64 only for the block sum)
     // lane j of a group preloads the coordinates of the group's j-th visibility,
     // so the 8 coordinate loads of a group are in flight together
     int pcx = 0, pcy = 0;
@@ -104,64 +104,78 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
         const int64_t ip = beg + grp + 32 * j;
         if (ip < end) VisCoord<R>::get(a.coords, ip, a.g, pcx, pcy, pfx, pfy);
     }
-#pragma unroll 2
-    for (int it = 0; it < DEGRID_CHUNK / 32; ++it) {
-        const int64_t iv = beg + grp + 32 * it;
-        const bool valid = iv < end;
-        const int64_t i = valid ? iv : beg;
-        const int src = gbase + it;
-        const int cxv = __shfl_sync(0xffffffffu, pcx, src);
-        const int cyv = __shfl_sync(0xffffffffu, pcy, src);
-        const R fx = __shfl_sync(0xffffffffu, pfx, src);
-        const R fy = __shfl_sync(0xffffffffu, pfy, src);
-        const int k0x = (cxv - 3) & (Kx - 1);
-        const int k0y = (cyv - 3) & (Ky - 1);
-        const R pu = horner<R, NC>(c, (R)2 * fx - (R)1);
-        const R pv = horner<R, NC>(c, (R)2 * fy - (R)1);
-        const int col = (k0x + j) & (Kx - 1);
-        CT acc = cx<R>(0, 0);
+    // two visibilities per group and step: their 16 grid loads are issued together
+    for (int it = 0; it < DEGRID_CHUNK / 32; it += 2) {
+        int col[2], k0y[2];
+        R pu[2], pv[2];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int row = (k0y + r) & (Ky - 1);
-            const CT gv = G[(int64_t)row * Kx + col];
-            const R pvr = __shfl_sync(0xffffffffu, pv, gbase + r);
-            acc.x = fma(pvr, gv.x, acc.x);
-            acc.y = fma(pvr, gv.y, acc.y);
+        for (int h = 0; h < 2; ++h) {
+            const int src = gbase + it + h;
+            const int cxv = __shfl_sync(0xffffffffu, pcx, src);
+            const int cyv = __shfl_sync(0xffffffffu, pcy, src);
+            const R fx = __shfl_sync(0xffffffffu, pfx, src);
+            const R fy = __shfl_sync(0xffffffffu, pfy, src);
+            col[h] = (((cxv - 3) & (Kx - 1)) + j) & (Kx - 1);
+            k0y[h] = (cyv - 3) & (Ky - 1);
+            pu[h] = horner<R, NC>(c, (R)2 * fx - (R)1);
+            pv[h] = horner<R, NC>(c, (R)2 * fy - (R)1);
         }
-        acc.x *= pu;
-        acc.y *= pu;
+        CT gv[2][8];
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) gv[h][r] = G[(int64_t)((k0y[h] + r) & (Ky - 1)) * Kx + col[h]];
+        CT acc[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            acc[h] = cx<R>(0, 0);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const R pvr = __shfl_sync(0xffffffffu, pv[h], gbase + r);
+                acc[h].x = fma(pvr, gv[h][r].x, acc[h].x);
+                acc[h].y = fma(pvr, gv[h][r].y, acc[h].y);
+            }
+            acc[h].x *= pu[h];
+            acc[h].y *= pu[h];
         }
-        if (valid && j == 0) {
-            if (a.w) acc = cscale(acc, a.w[i]);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                acc[h].x += __shfl_xor_sync(0xffffffffu, acc[h].x, o);
+                acc[h].y += __shfl_xor_sync(0xffffffffu, acc[h].y, o);
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = beg + grp + 32 * (it + h);
+            if (i >= end || j != 0) continue;
+            CT v = acc[h];
+            if (a.w) v = cscale(v, a.w[i]);
             if (MODE == DOUT_CALLER) {
-                a.out[a.perm[i]] = acc;
+                a.out[a.perm[i]] = v;
             } else if (MODE == DOUT_SORTED) {
-                a.out[i] = acc;
+                a.out[i] = v;
             } else if (MODE == DOUT_SORTED_U) {
-                a.out[i] = a.u ? cscale(acc, a.u[i]) : acc;
+                a.out[i] = a.u ? cscale(v, a.u[i]) : v;
             } else {   // DOUT_PD: vbar = v + U Phi x~, d = U^{-1/2} vbar - y
                 CT vb = a.v[i];
                 CT dd;
                 if (a.u) {
                     const R uu = a.u[i];
                     const R is = (R)1 / sqrt(uu);
-                    vb.x = fma(uu, acc.x, vb.x);
-                    vb.y = fma(uu, acc.y, vb.y);
+                    vb.x = fma(uu, v.x, vb.x);
+                    vb.y = fma(uu, v.y, vb.y);
                     dd = csub(cscale(vb, is), a.y[i]);
                 } else {
-                    dd = csub(cadd(vb, acc), a.y[i]);
+                    dd = csub(cadd(vb, v), a.y[i]);
                 }
                 a.d[i] = dd;
-                sq += (double)dd.x * (double)dd.x + (double)dd.y * (double)dd.y;
+                sq = fma(dd.x, dd.x, fma(dd.y, dd.y, sq));
             }
         }
     }
     if (MODE == DOUT_PD) {
-        const double tot = block_sum(sq, red);
+        const double tot = block_sum((double)sq, red);
         if (threadIdx.x == 0) a.part[(int64_t)l * a.nblk_x + blockIdx.x] = tot;
     }
 }

@@ -233,7 +233,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
     std::vector<int> gent;
     gent.reserve((size_t)(toff.back() + toff.back() / 4 + 64));
     {
-        constexpr int GROUP_OPEN = 8;
+        constexpr int GROUP_OPEN = 64;
         struct Group {
             int m;
             int e[4], x[4], y[4];

@@ -380,7 +380,7 @@ __global__ void k_primal(int64_t n, const R* __restrict__ P, const R* __restrict
                          const R* __restrict__ D, R k1, R k2, R k3, R tau, R* __restrict__ X,
                          R* __restrict__ Xt, double* __restrict__ part) {
     __shared__ double red[32];
-    double dd = 0.0, xx = 0.0;
+    R ddr = 0, xxr = 0;   // this thread's sums (few terms); FP64 for the block sums
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         R g = k3 * D[i];
@@ -391,12 +391,12 @@ __global__ void k_primal(int64_t n, const R* __restrict__ P, const R* __restrict
         xn = xn > (R)0 ? xn : (R)0;
         X[i] = xn;
         Xt[i] = (R)2 * xn - xo;
-        const double df = (double)xn - (double)xo;
-        dd += df * df;
-        xx += (double)xn * (double)xn;
+        const R df = xn - xo;
+        ddr = fma(df, df, ddr);
+        xxr = fma(xn, xn, xxr);
     }
-    dd = block_sum(dd, red);
-    xx = block_sum(xx, red);
+    const double dd = block_sum((double)ddr, red);
+    const double xx = block_sum((double)xxr, red);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = dd;
         part[2 * blockIdx.x + 1] = xx;
