@@ -21,7 +21,8 @@
 //  3. Modified Gram-Schmidt, then an FP64 Rayleigh-Ritz step on the active
 //     subspace (FP64 Jacobi on the r x r matrix X^T S X) resolves the
 //     eigenpairs inside it.
-//  4. Mf = I - sum_active (1 - f) x x^T (dual) or sum_active f x x^T (prox).
+//  4. The factor is returned in low-rank form: M = I - sum_active (1 - f) x x^T
+//     (dual) or sum_active f x x^T (prox), as r, g and the active x.
 #include <cmath>
 
 #include "hs_device.cuh"
@@ -37,44 +38,51 @@ __device__ __forceinline__ double eig_bsum(double v, double* red) { return block
 
 // Round-robin (circle method) schedule for n indices, n even: in round r the
 // index n-1 meets r and (r + i) meets (r - i) (mod n-1) for i = 1 .. n/2-1.
-// partner[r * n + i] is the index paired with i in round r.
-__device__ void rr_schedule(int n, signed char* partner) {
-    for (int k = threadIdx.x; k < (n - 1) * n; k += blockDim.x) {
-        const int r = k / n, i = k - r * n;
-        int pi;
-        if (i == n - 1) pi = r;
-        else if (i == r) pi = n - 1;
-        else pi = ((2 * r - i) % (n - 1) + (n - 1)) % (n - 1);
-        partner[k] = (signed char)pi;
+// pairs[r * n + 2 k], pairs[r * n + 2 k + 1] = (p, q), p < q, is the k-th
+// pair of round r (thread r lists its round).
+__device__ void rr_schedule(int n, unsigned char* pairs) {
+    for (int r = threadIdx.x; r < n - 1; r += blockDim.x) {
+        int k = 0;
+        for (int i = 0; i < n; ++i) {
+            int pi;
+            if (i == n - 1) pi = r;
+            else if (i == r) pi = n - 1;
+            else pi = ((2 * r - i) % (n - 1) + (n - 1)) % (n - 1);
+            if (i < pi) {
+                pairs[r * n + 2 * k] = (unsigned char)i;
+                pairs[r * n + 2 * k + 1] = (unsigned char)pi;
+                ++k;
+            }
+        }
     }
 }
 
 // Cyclic Jacobi, round-robin parallel ordering, on the symmetric N x N matrix
-// in A (leading dimension LDJ), accumulating V <- V J; B and W are scratch of
-// the same shape. Each round, every index i computes the rotation of its pair
-// (p, q) from a_pp, a_qq, a_pq (symmetric Schur decomposition, Golub & Van Loan
-// Alg. 8.4.1), then every entry is updated at once from four old entries:
-//   A'_ij = c_i c_j A_ij + c_i t_j A_i,pj + t_i c_j A_pi,j + t_i t_j A_pi,pj,
-//   V'_kj = c_j V_kj + t_j V_k,pj,
-// with t_p = -s, t_q = +s (J_pp = J_qq = c, J_pq = s, J_qp = -s). A rotation is
-// applied only when |a_pq| exceeds skip sqrt(|a_pp a_qq|) and floor_rel ||A||_F;
-// sweeps stop when the off-diagonal Frobenius norm is at most off_rel ||A||_F,
-// when a sweep applies no rotation, or after max_sweeps. The result is left
-// in A and V.
+// in A (leading dimension LDJ), accumulating V <- V J. Each round, thread k < N/2
+// computes the rotation of pair k = (p, q) from a_pp, a_qq, a_pq (symmetric
+// Schur decomposition, Golub & Van Loan Alg. 8.4.1: J_pp = J_qq = c,
+// J_pq = s, J_qp = -s); then thread (i, j) of the (N/2)^2 block grid applies
+// A <- J^T A J to the 2 x 2 block (rows of pair i, columns of pair j):
+//   rows   (p, q) <- (c_i row_p - s_i row_q, s_i row_p + c_i row_q)
+//   cols   (p, q) <- (c_j col_p - s_j col_q, s_j col_p + c_j col_q),
+// and the columns of V are rotated the same way. Every entry belongs to one
+// thread per round, so A and V are updated in place (4 loads and 4 stores per
+// block). A rotation is applied only when |a_pq| exceeds skip sqrt(|a_pp a_qq|)
+// and floor_rel ||A||_F; sweeps stop when the off-diagonal Frobenius norm is at
+// most off_rel ||A||_F, when a sweep applies no rotation, or after max_sweeps.
 template <typename T, int N>
-__device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partner, double skip,
-                                double floor_rel, double off_rel, int max_sweeps, T* cvec, T* tvec,
-                                double* red, int* flag) {
+__device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double skip, double floor_rel,
+                              double off_rel, int max_sweeps, T* cvec, T* svec, double* red, int* flag) {
     constexpr int LDJ = MAX_L_NUC + 1;
+    constexpr int NP = N / 2;
     constexpr int LG = (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
-    T *a = A, *b = B, *v = V, *w = W;
     const T skipT = (T)skip;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         T nrmT = 0, offT = 0;   // per-thread partial sums in the working precision
         for (int k = tid; k < N * N; k += nt) {
             const int i = k >> LG, j = k & (N - 1);
-            const T x = a[i * LDJ + j];
+            const T x = A[i * LDJ + j];
             nrmT = fma(x, x, nrmT);
             if (i != j) offT = fma(x, x, offT);
         }
@@ -85,11 +93,10 @@ __device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partn
         if (tid == 0) *flag = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
-            const signed char* pr = partner + r * N;
-            if (tid < N) {
-                const int i = tid, pi = pr[i];
-                const int p = i < pi ? i : pi, q = i < pi ? pi : i;
-                const T apq = a[p * LDJ + q], app = a[p * LDJ + p], aqq = a[q * LDJ + q];
+            const unsigned char* pr = pairs + r * N;
+            if (tid < NP) {
+                const int p = pr[2 * tid], q = pr[2 * tid + 1];
+                const T apq = A[p * LDJ + q], app = A[p * LDJ + p], aqq = A[q * LDJ + q];
                 T c = 1, s = 0;
                 const T ab = fabs(apq);
                 if (ab > flo && ab > T(0) && ab > skipT * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
@@ -99,64 +106,57 @@ __device__ void jacobi_pairwise(T* A, T* B, T* V, T* W, const signed char* partn
                     s = t * c;
                     *flag = 1;
                 }
-                cvec[i] = c;
-                tvec[i] = (i == p) ? -s : s;
+                cvec[tid] = c;
+                svec[tid] = s;
             }
             __syncthreads();
-            for (int k = tid; k < 2 * N * N; k += nt) {
-                const int kk = k & (N * N - 1);
-                const int i = kk >> LG, j = kk & (N - 1);
-                const int pj = pr[j];
-                const T cj = cvec[j], tj = tvec[j];
-                if (k < N * N) {
-                    const int pi = pr[i];
-                    const T ci = cvec[i], ti = tvec[i];
-                    T x = ci * cj * a[i * LDJ + j];
-                    if (tj != T(0)) x = fma(ci * tj, a[i * LDJ + pj], x);
-                    if (ti != T(0)) {
-                        x = fma(ti * cj, a[pi * LDJ + j], x);
-                        if (tj != T(0)) x = fma(ti * tj, a[pi * LDJ + pj], x);
-                    }
-                    if (j == pi && ti != T(0)) x = T(0);   // the rotated pair is decoupled
-                    b[i * LDJ + j] = x;
-                } else {
-                    T x = cj * v[i * LDJ + j];
-                    if (tj != T(0)) x = fma(tj, v[i * LDJ + pj], x);
-                    w[i * LDJ + j] = x;
+            if (tid < NP * NP) {
+                const int bi = tid / NP, bj = tid - bi * NP;
+                const int pi = pr[2 * bi], qi = pr[2 * bi + 1], pj = pr[2 * bj], qj = pr[2 * bj + 1];
+                const T ci = cvec[bi], si = svec[bi], cj = cvec[bj], sj = svec[bj];
+                const T a00 = A[pi * LDJ + pj], a01 = A[pi * LDJ + qj];
+                const T a10 = A[qi * LDJ + pj], a11 = A[qi * LDJ + qj];
+                const T r0x = ci * a00 - si * a10, r0y = ci * a01 - si * a11;
+                const T r1x = si * a00 + ci * a10, r1y = si * a01 + ci * a11;
+                T b00 = cj * r0x - sj * r0y, b01 = sj * r0x + cj * r0y;
+                T b10 = cj * r1x - sj * r1y, b11 = sj * r1x + cj * r1y;
+                if (bi == bj && si != T(0)) {   // the rotated pair is decoupled
+                    b01 = T(0);
+                    b10 = T(0);
                 }
+                A[pi * LDJ + pj] = b00;
+                A[pi * LDJ + qj] = b01;
+                A[qi * LDJ + pj] = b10;
+                A[qi * LDJ + qj] = b11;
+            }
+            for (int u = tid; u < N * NP; u += nt) {
+                const int k = u / NP, j = u - k * NP;
+                const int p = pr[2 * j], q = pr[2 * j + 1];
+                const T c = cvec[j], s = svec[j];
+                const T v0 = V[k * LDJ + p], v1 = V[k * LDJ + q];
+                V[k * LDJ + p] = c * v0 - s * v1;
+                V[k * LDJ + q] = s * v0 + c * v1;
             }
             __syncthreads();
-            T* t1 = a;
-            a = b;
-            b = t1;
-            t1 = v;
-            v = w;
-            w = t1;
         }
         const int any = *flag;
         __syncthreads();
         if (!any) break;
     }
-    if (a != A) {   // leave the result in A / V
-        for (int k = tid; k < N * N; k += nt) {
-            const int i = k >> LG, j = k & (N - 1);
-            A[i * LDJ + j] = a[i * LDJ + j];
-            V[i * LDJ + j] = v[i * LDJ + j];
-        }
-        __syncthreads();
-    }
 }
 
-// Dispatch on the padded size n (power of two, 2..64).
+// Dispatch on the padded size n (power of two, 2..64). B and W are unused
+// scratch kept for the callers' layouts.
 template <typename T>
-__device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, signed char* partner, double skip,
+__device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, unsigned char* pairs, double skip,
                          double floor_rel, double off_rel, int max_sweeps, T* cvec, T* tvec,
                          double* red, int* flag) {
-    rr_schedule(n, partner);
+    (void)B;
+    (void)W;
+    rr_schedule(n, pairs);
     __syncthreads();
-#define HS_JAC(NN)                                                                                   \
-    jacobi_pairwise<T, NN>(A, B, V, W, partner, skip, floor_rel, off_rel, max_sweeps, cvec, tvec, red, \
-                           flag)
+#define HS_JAC(NN) \
+    jacobi_blocks<T, NN>(A, V, pairs, skip, floor_rel, off_rel, max_sweeps, cvec, tvec, red, flag)
     switch (n) {
         case 2: HS_JAC(2); break;
         case 4: HS_JAC(4); break;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     __shared__ double red[33];
     __shared__ float cv32[MAX_L_NUC], tv32[MAX_L_NUC];
     __shared__ double cv64[MAX_L_NUC], tv64[MAX_L_NUC];
-    __shared__ signed char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ unsigned char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
     __shared__ int flag;
     __shared__ double lam32[MAX_L_NUC], lamr[MAX_L_NUC], fv[MAX_L_NUC];
     __shared__ int order[MAX_L_NUC], ordr[MAX_L_NUC];
@@ -418,15 +418,15 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     }
     if (sv_out)
         for (int j = r + tid; j < L; j += nt) sv_out[j] = sqrt(fmax(lam32[order[j]], 0.0));
-    // ---- 4. Mf
-    for (int k = tid; k < L * L; k += nt) {
-        const int i = k / L, m = k - i * L;
-        double acc = dual ? (i == m ? 1.0 : 0.0) : 0.0;
-        for (int c = 0; c < r; ++c) {
-            const double g = dual ? (lamr[c] - 1.0) : lamr[c];
-            acc = fma(g * Y[i * MAX_L_NUC + c], Y[m * MAX_L_NUC + c], acc);
-        }
-        Mf[i * L + m] = acc;
+    // ---- 4. low-rank factor: M = I + sum_c (f_c - 1) y_c y_c^T (dual) or sum_c f_c y_c y_c^T
+    if (tid == 0) {
+        Mf[LR_R] = (double)r;
+        Mf[LR_BASE] = dual ? 1.0 : 0.0;
+    }
+    if (tid < r) Mf[LR_G + tid] = dual ? lamr[tid] - 1.0 : lamr[tid];
+    for (int k = tid; k < L * r; k += nt) {
+        const int i = k / r, c = k - i * r;
+        Mf[LR_X + c * MAX_L_NUC + i] = Y[i * MAX_L_NUC + c];
     }
 }
 
@@ -435,7 +435,7 @@ size_t eig_mixed_smem() {
 }
 
 // FP64 plans: the whole Gram matrix is diagonalised by the FP64 Jacobi method;
-// f and Mf as in k_eig_mixed (all eigenpairs are FP64-accurate).
+// f and the low-rank factor as in k_eig_mixed (all eigenpairs are FP64-accurate).
 __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg, int L,
                                                   const double* __restrict__ w_sv, double thr, int dual,
                                                   double* __restrict__ Mf, double* __restrict__ sv_out,
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg
     __shared__ double red[33];
     __shared__ double cv[MAX_L_NUC], tv[MAX_L_NUC], lam[MAX_L_NUC], fv[MAX_L_NUC];
     __shared__ int order[MAX_L_NUC];
-    __shared__ signed char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ unsigned char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
     __shared__ int flag;
     const int tid = threadIdx.x, nt = blockDim.x;
     int n = 2;
@@ -485,11 +485,22 @@ __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg
         if (r_out) *r_out = r;
     }
     __syncthreads();
-    for (int k = tid; k < L * L; k += nt) {
-        const int i = k / L, m = k - i * L;
-        double acc = 0.0;
-        for (int j = 0; j < L; ++j) acc = fma(V[i * LD32 + order[j]] * fv[j], V[m * LD32 + order[j]], acc);
-        Mf[i * L + m] = acc;
+    // low-rank factor over the pairs with sigma > c (f differs from its limit only there)
+    __shared__ int r_act;
+    if (tid == 0) {
+        int r = 0;
+        for (int j = 0; j < L; ++j)
+            if (sqrt(fmax(lam[order[j]], 0.0)) > thr * (w_sv ? w_sv[j] : 1.0)) r = j + 1;
+        r_act = r;
+        Mf[LR_R] = (double)r;
+        Mf[LR_BASE] = dual ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int r = r_act;
+    if (tid < r) Mf[LR_G + tid] = dual ? fv[tid] - 1.0 : fv[tid];
+    for (int k = tid; k < L * r; k += nt) {
+        const int i = k / r, c = k - i * r;
+        Mf[LR_X + c * MAX_L_NUC + i] = V[i * LD32 + order[c]];
     }
 }
 

@@ -43,6 +43,11 @@ constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumula
 constexpr int GRID_CAP = 512;        // most list entries one gridding CTA processes
 constexpr int DEGRID_CHUNK = 256;    // visibilities per degridding CTA
 constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
+// Low-rank form of the nuclear prox factor M = base I + sum_c g_c x_c x_c^T
+// (doubles in Plan::eigf): [LR_R] active count r, [LR_BASE] 1 (dual) or 0,
+// [LR_G + c] g_c, [LR_X + c * MAX_L_NUC + i] component i of x_c.
+constexpr int LR_R = 0, LR_BASE = 1, LR_G = 2, LR_X = 2 + MAX_L_NUC;
+constexpr int LR_DOUBLES = LR_X + MAX_L_NUC * MAX_L_NUC;
 
 // Coordinates of one visibility in an FP64 plan: window start cells and the
 // fractional part of t = u K / (2 pi) (exact in FP64).
@@ -100,7 +105,7 @@ struct Plan {
     double* part = nullptr;            // partial sums (size part_n doubles)
     int64_t part_n = 0;
     double* gram = nullptr;            // MAX_L_NUC^2 doubles
-    double* eigf = nullptr;            // MAX_L_NUC^2 doubles (factor matrix V diag(f) V^T)
+    double* eigf = nullptr;            // LR_DOUBLES: low-rank prox factor (layout above)
     double* sv = nullptr;              // MAX_L_NUC doubles
     double* dscal = nullptr;           // small per-channel doubles (4 * L)
     void* xbuf = nullptr;              // L * N reals (power iteration, misc)

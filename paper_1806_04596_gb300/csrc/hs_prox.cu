@@ -31,29 +31,54 @@ __global__ void k_reduce_rows(const double* __restrict__ part, int nb, double* _
 }
 
 // ---------------------------------------------------------------- l2,1
-template <typename R>
-__global__ void k_l21(const R* __restrict__ A, const R* __restrict__ W, const R* __restrict__ w_rows,
-                      R thr, int dual, R* __restrict__ out, int L, int64_t N) {
+// One thread per row (basis b, pixel n) of the coefficient cube: q_l = A + W
+// over the L channels (stride N), the row norm, and the scaled row. For
+// L <= LMAX the row is held in registers (each input read once); LMAX = 0 is
+// the general form that reads the row twice.
+template <typename R, int LMAX>
+__global__ void __launch_bounds__(256) k_l21(const R* __restrict__ A, const R* __restrict__ W,
+                                             const R* __restrict__ w_rows, R thr, int dual,
+                                             R* __restrict__ out, int L, int64_t N) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)NB * N) return;
     const int b = (int)(t / N);
     const int64_t pix = t - (int64_t)b * N;
     const int64_t base = (int64_t)b * L * N + pix;
     R s = 0;
-    for (int l = 0; l < L; ++l) {
-        R q = A[base + (int64_t)l * N];
-        if (W) q += W[base + (int64_t)l * N];
-        s = fma(q, q, s);
+    R q[LMAX > 0 ? LMAX : 1];
+    if (LMAX > 0) {
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l)
+            if (l < L) {
+                R v = A[base + (int64_t)l * N];
+                if (W) v += W[base + (int64_t)l * N];
+                q[l] = v;
+            }
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l)
+            if (l < L) s = fma(q[l], q[l], s);
+    } else {
+        for (int l = 0; l < L; ++l) {
+            R v = A[base + (int64_t)l * N];
+            if (W) v += W[base + (int64_t)l * N];
+            s = fma(v, v, s);
+        }
     }
     const R nrm = sqrt(s);
     const R lam = thr * (w_rows ? w_rows[t] : (R)1);
     R f;
     if (dual) f = (nrm > lam) ? lam / nrm : (R)1;
     else f = (nrm > lam) ? (nrm - lam) / nrm : (R)0;
-    for (int l = 0; l < L; ++l) {
-        R q = A[base + (int64_t)l * N];
-        if (W) q += W[base + (int64_t)l * N];
-        out[base + (int64_t)l * N] = q * f;
+    if (LMAX > 0) {
+#pragma unroll
+        for (int l = 0; l < LMAX; ++l)
+            if (l < L) out[base + (int64_t)l * N] = q[l] * f;
+    } else {
+        for (int l = 0; l < L; ++l) {
+            R v = A[base + (int64_t)l * N];
+            if (W) v += W[base + (int64_t)l * N];
+            out[base + (int64_t)l * N] = v * f;
+        }
     }
 }
 
@@ -82,12 +107,20 @@ hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows
                     int dual, void* out, cudaStream_t s) {
     const int64_t N = p->N();
     const unsigned g = nblk((int64_t)NB * N, 256);
-    if (p->prec == HS_F32)
-        k_l21<float><<<g, 256, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
-                                       (float)thr, dual, (float*)out, p->g.L, N);
-    else
-        k_l21<double><<<g, 256, 0, s>>>((const double*)A, (const double*)Wadd,
-                                        (const double*)w_rows, thr, dual, (double*)out, p->g.L, N);
+    const int L = p->g.L;
+#define HS_L21(R, LM)                                                                                    \
+    k_l21<R, LM><<<g, 256, 0, s>>>((const R*)A, (const R*)Wadd, (const R*)w_rows, (R)thr, dual, (R*)out, L, \
+                                   N)
+    if (p->prec == HS_F32) {
+        if (L <= 16) HS_L21(float, 16);
+        else if (L <= 64) HS_L21(float, 64);
+        else HS_L21(float, 0);
+    } else {
+        if (L <= 16) HS_L21(double, 16);
+        else if (L <= 64) HS_L21(double, 64);
+        else HS_L21(double, 0);
+    }
+#undef HS_L21
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
@@ -204,66 +237,93 @@ hs_status ball_project(Plan* p, const void* Z, const void* Yd, const double* eps
 }
 
 // ---------------------------------------------------------------- nuclear norm
-constexpr int GRAM_ROWS = 32;     // pixels per shared-memory tile (R sums, then FP64)
+constexpr int GRAM_PIX = 64;      // pixels per shared-memory tile
 constexpr int GRAM_CTAS = 304;    // 2 per SM
-constexpr int GRAM_PER = 9;       // upper-triangle entries per thread (256 threads, L <= 64)
+constexpr int GRAM_LDZ = MAX_L_NUC + 4;   // pixel-major tile row (16-byte aligned)
 
-// Partial Gram matrices: CTA c accumulates sum over its pixel tiles of z z^T for
-// the upper triangle (i <= j), tile sums in R, running sum in FP64.
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+    const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = t0.x;
+    v[1] = t0.y;
+    v[2] = t1.x;
+    v[3] = t1.y;
+}
+
+// Partial Gram matrices S_ij = sum_n z_in z_jn, z = X (+ Xa), for L <= 64:
+// thread (bi, bj) of a 16 x 16 grid owns the 4 x 4 block of rows 4 bi .. 4 bi + 3
+// and columns 4 bj .. 4 bj + 3 (register blocking: per pixel two 4-wide shared
+// loads feed 16 FMAs). Runs of 32 pixels are summed in R and added into a
+// (hi, lo) pair with the error-free two-sum (Knuth), so the accumulation across
+// runs is as exact as in FP64 without FP64 arithmetic; each CTA writes its
+// upper-triangle partials in FP64.
 template <typename R>
 __global__ void __launch_bounds__(256) k_gram(const R* __restrict__ X, const R* __restrict__ Xa,
                                               int L, int64_t N, double* __restrict__ part) {
-    __shared__ R zs[GRAM_ROWS][MAX_L_NUC + 1];
-    const int P = L * (L + 1) / 2;
-    int pi[GRAM_PER], pj[GRAM_PER];
-    double acc[GRAM_PER];
+    __shared__ __align__(16) R zs[GRAM_PIX][GRAM_LDZ];   // pixel-major tile
+    const int tid = threadIdx.x;
+    const int bi = tid >> 4, bj = tid & 15;
+    R hi[16], lo[16];
 #pragma unroll
-    for (int q = 0; q < GRAM_PER; ++q) {
-        const int e = threadIdx.x + q * 256;
-        acc[q] = 0.0;
-        pi[q] = 0;
-        pj[q] = 0;
-        if (e < P) {   // unrank e -> (i, j), i <= j, row-major over the upper triangle
-            int i = 0, rem = e;
-            while (rem >= L - i) {
-                rem -= L - i;
-                ++i;
-            }
-            pi[q] = i;
-            pj[q] = i + rem;
-        }
+    for (int q = 0; q < 16; ++q) {
+        hi[q] = 0;
+        lo[q] = 0;
     }
-    const int64_t ntile = (N + GRAM_ROWS - 1) / GRAM_ROWS;
+    const int64_t ntile = N / GRAM_PIX;   // N is a multiple of 64 (nx, ny >= 16, powers of two)
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t n0 = tile * GRAM_ROWS;
+        const int64_t n0 = tile * GRAM_PIX;
         __syncthreads();
-        for (int k = threadIdx.x; k < GRAM_ROWS * L; k += 256) {
-            const int l = k / GRAM_ROWS, r = k - l * GRAM_ROWS;
-            const int64_t n = n0 + r;
+        for (int k = tid; k < MAX_L_NUC * GRAM_PIX; k += 256) {
+            const int l = k >> 6, px = k & (GRAM_PIX - 1);
             R z = 0;
-            if (n < N) {
-                z = X[(int64_t)l * N + n];
-                if (Xa) z += Xa[(int64_t)l * N + n];
+            if (l < L) {
+                z = X[(int64_t)l * N + n0 + px];
+                if (Xa) z += Xa[(int64_t)l * N + n0 + px];
             }
-            zs[r][l] = z;
+            zs[px][l] = z;
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < GRAM_PER; ++q) {
-            if (threadIdx.x + q * 256 < P) {
-                R s = 0;
-                const int i = pi[q], j = pj[q];
-#pragma unroll 8
-                for (int r = 0; r < GRAM_ROWS; ++r) s = fma(zs[r][i], zs[r][j], s);
-                acc[q] += (double)s;
+        for (int half = 0; half < GRAM_PIX / 32; ++half) {
+            R acc[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[q] = 0;
+#pragma unroll 4
+            for (int px = 32 * half; px < 32 * half + 32; ++px) {
+                R a[4], b[4];
+                ld4(&zs[px][4 * bi], a);
+                ld4(&zs[px][4 * bj], b);
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[4 * t + u] = fma(a[t], b[u], acc[4 * t + u]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {   // (hi, lo) += acc, hi + e = old hi + acc exactly
+                const R sum = hi[q] + acc[q];
+                const R bp = sum - hi[q];
+                const R e = (hi[q] - (sum - bp)) + (acc[q] - bp);
+                hi[q] = sum;
+                lo[q] += e;
             }
         }
     }
 #pragma unroll
-    for (int q = 0; q < GRAM_PER; ++q) {
-        const int e = threadIdx.x + q * 256;
-        if (e < P) part[(int64_t)e * gridDim.x + blockIdx.x] = acc[q];
-    }
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = 4 * bi + t, j = 4 * bj + u;
+            if (i <= j && j < L) {
+                const int e = i * L - i * (i - 1) / 2 + (j - i);   // row-major rank in the upper triangle
+                part[(int64_t)e * gridDim.x + blockIdx.x] = (double)hi[4 * t + u] + (double)lo[4 * t + u];
+            }
+        }
 }
 
 // Sum the per-CTA partials (fixed order) and expand to the full symmetric matrix.
@@ -285,28 +345,35 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int L, do
     }
 }
 
-// out[:, m] = sum_i Z[:, i] Mf[i, m] with Z = X + Xa, one thread per pixel,
-// the pixel's L values in registers, Mf broadcast from shared memory. In FP32
-// the FP64 factor matrix is carried as two FP32 parts (hi + lo), so that its
-// rounding does not enter the result: the output is often a small remainder of
-// a large Z (the dual form keeps the small singular values).
+// out[:, n] = M z_n with z = X (+ Xa) and M = base I + sum_{c < r} g_c x_c x_c^T
+// (low-rank form written by the eigensolver): per pixel, r projections
+// p_c = x_c . z and the update out = base z + sum_c (g_c p_c) x_c, the pixel's
+// L values in registers and x_c broadcast from shared memory. In FP32 the FP64
+// vectors are carried as two FP32 parts (hi + lo), so that their rounding does
+// not enter the result: the output is often a small remainder of a large z
+// (the dual form keeps the small singular values).
 template <typename R, int LMAX>
 __global__ void __launch_bounds__(128) k_lowrank_apply(const R* __restrict__ X,
                                                        const R* __restrict__ Xa,
-                                                       const double* __restrict__ Mf, int L,
+                                                       const double* __restrict__ F, int L,
                                                        int64_t N, R* __restrict__ out) {
     constexpr bool SPLIT = sizeof(R) == 4;
-    __shared__ R Ms[LMAX * LMAX];
-    __shared__ R Ml[SPLIT ? LMAX * LMAX : 1];
-    for (int k = threadIdx.x; k < L * L; k += blockDim.x) {
-        const double m = Mf[k];
-        Ms[k] = (R)m;
-        if (SPLIT) Ml[k] = (R)(m - (double)(R)m);
+    __shared__ R xh[LMAX * LMAX];
+    __shared__ R xl[SPLIT ? LMAX * LMAX : 1];
+    __shared__ R gs[LMAX];
+    const int r = (int)F[LR_R];
+    const bool base = F[LR_BASE] != 0.0;
+    for (int k = threadIdx.x; k < r * L; k += blockDim.x) {
+        const int c = k / L, i = k - c * L;
+        const double v = F[LR_X + c * MAX_L_NUC + i];
+        xh[c * LMAX + i] = (R)v;
+        if (SPLIT) xl[c * LMAX + i] = (R)(v - (double)(R)v);
     }
+    if (threadIdx.x < r) gs[threadIdx.x] = (R)F[LR_G + threadIdx.x];
     __syncthreads();
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n >= N) return;
-    R z[LMAX];
+    R z[LMAX], o[LMAX];
 #pragma unroll
     for (int i = 0; i < LMAX; ++i) {
         z[i] = 0;
@@ -314,17 +381,29 @@ __global__ void __launch_bounds__(128) k_lowrank_apply(const R* __restrict__ X,
             z[i] = X[(int64_t)i * N + n];
             if (Xa) z[i] += Xa[(int64_t)i * N + n];
         }
+        o[i] = base ? z[i] : (R)0;
     }
-    for (int m = 0; m < L; ++m) {
-        R acc = 0, acc2 = 0;
+    for (int c = 0; c < r; ++c) {
+        const R* h = xh + c * LMAX;
+        const R* lo = xl + (SPLIT ? c * LMAX : 0);
+        R p = 0, p2 = 0;
 #pragma unroll
         for (int i = 0; i < LMAX; ++i)
             if (i < L) {
-                acc = fma(z[i], Ms[i * L + m], acc);
-                if (SPLIT) acc2 = fma(z[i], Ml[i * L + m], acc2);
+                p = fma(z[i], h[i], p);
+                if (SPLIT) p2 = fma(z[i], lo[i], p2);
             }
-        out[(int64_t)m * N + n] = acc + acc2;
+        const R q = gs[c] * (p + p2);
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i)
+            if (i < L) {
+                o[i] = fma(q, h[i], o[i]);
+                if (SPLIT) o[i] = fma(q, lo[i], o[i]);
+            }
     }
+#pragma unroll
+    for (int i = 0; i < LMAX; ++i)
+        if (i < L) out[(int64_t)i * N + n] = o[i];
 }
 
 template <typename R>
