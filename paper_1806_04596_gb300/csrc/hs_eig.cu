@@ -11,14 +11,15 @@
 //     from the previous call's eigenvectors V0 (A = V0^T S V0), gives every
 //     eigenpair to FP32 accuracy.
 //  2. The active eigenvectors are refined in FP64 against the rest of the
-//     basis with two first-order correction steps of an approximate
-//     eigendecomposition (Ogita & Aishima 2018): with b_j the basis, T = B^T S X,
+//     basis with first-order correction steps (one from a warm basis, two
+//     cold) of an approximate eigendecomposition (Ogita & Aishima 2018): with
+//     b_j the basis, T = B^T S X,
 //     R = I - B^T X, lambda_c = T_cc / (1 - R_cc), the correction of x_c along
 //     b_j is (T_jc + lambda_c R_jc) / (lambda_c - lambda_j) across the active /
 //     inactive boundary and R_jc / 2 (orthogonalisation only) inside the active
 //     set or for near-equal eigenvalues (those straddle the threshold, where f
 //     is continuous, so their mixing does not change the result).
-//  3. Modified Gram-Schmidt, then an FP64 Rayleigh-Ritz step on the active
+//  3. Cholesky QR, then an FP64 Rayleigh-Ritz step on the active
 //     subspace (FP64 Jacobi on the r x r matrix X^T S X) resolves the
 //     eigenpairs inside it.
 //  4. The factor is returned in low-rank form: M = I - sum_active (1 - f) x x^T
@@ -57,6 +58,22 @@ __device__ void rr_schedule(int n, unsigned char* pairs) {
     }
 }
 
+// Rotation (c, s) that zeroes a_pq of the 2 x 2 block [[a_pp, a_pq], [a_pq, a_qq]]
+// (Golub & Van Loan Alg. 8.4.1). FP32: fast reciprocal and reciprocal square
+// root (the FP32 sweeps only need FP32-orthogonal rotations); FP64: IEEE.
+__device__ __forceinline__ void jac_rot(float app, float aqq, float apq, float& c, float& s) {
+    const float tau = __fdividef(aqq - app, 2.f * apq);
+    const float t = copysignf(1.f, tau) * __frcp_rn(fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = t * c;
+}
+__device__ __forceinline__ void jac_rot(double app, double aqq, double apq, double& c, double& s) {
+    const double tau = (aqq - app) / (2.0 * apq);
+    const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+    c = rsqrt(fma(t, t, 1.0));
+    s = t * c;
+}
+
 // Cyclic Jacobi, round-robin parallel ordering, on the symmetric N x N matrix
 // in A (leading dimension LDJ), accumulating V <- V J. Each round, thread k < N/2
 // computes the rotation of pair k = (p, q) from a_pp, a_qq, a_pq (symmetric
@@ -77,7 +94,7 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
     constexpr int NP = N / 2;
     constexpr int LG = (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const T skipT = (T)skip;
+    const T skip2 = (T)(skip * skip);
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         T nrmT = 0, offT = 0;   // per-thread partial sums in the working precision
         for (int k = tid; k < N * N; k += nt) {
@@ -99,11 +116,8 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
                 const T apq = A[p * LDJ + q], app = A[p * LDJ + p], aqq = A[q * LDJ + q];
                 T c = 1, s = 0;
                 const T ab = fabs(apq);
-                if (ab > flo && ab > T(0) && ab > skipT * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
-                    const T tau = (aqq - app) / (T(2) * apq);
-                    const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-                    c = T(1) / sqrt(T(1) + t * t);
-                    s = t * c;
+                if (ab > flo && ab * ab > skip2 * fabs(app * aqq)) {
+                    jac_rot(app, aqq, apq, c, s);
                     *flag = 1;
                 }
                 cvec[tid] = c;
@@ -194,6 +208,7 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     __shared__ unsigned char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
     __shared__ int flag;
     __shared__ double lam32[MAX_L_NUC], lamr[MAX_L_NUC], fv[MAX_L_NUC];
+    __shared__ float lamf[MAX_L_NUC];
     __shared__ int order[MAX_L_NUC], ordr[MAX_L_NUC];
     __shared__ int r_act;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -234,35 +249,31 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
         __syncthreads();
     }
     // ---- 1. FP32 Jacobi on every eigenpair
-    // warm-started calls run at most two FP32 sweeps: the active pairs are made
-    // exact in FP64 below, and the basis keeps improving from call to call
-    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 2 : 15, cv32, tv32, red, &flag);
+    // warm-started calls run one FP32 sweep: the active pairs are made exact in
+    // FP64 below, and the basis keeps improving from call to call
+    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 1 : 15, cv32, tv32, red, &flag);
     // ---- eigenvalues, descending order (rank by counting), warm start for the next call
-    if (tid < L) lam32[tid] = (double)A32[tid * LD32 + tid];
-    __syncthreads();
     if (tid < L) {
+        lamf[tid] = A32[tid * LD32 + tid];
+        lam32[tid] = (double)lamf[tid];
+    }
+    if (tid == 0) r_act = 0;
+    __syncthreads();
+    if (tid < L) {   // rank of eigenvalue tid; active when sigma > c_rank (1 - 1e-3)
         int rk = 0;
-        const double li = lam32[tid];
+        const float li = lamf[tid];
         for (int j = 0; j < L; ++j) {
-            const double lj = lam32[j];
+            const float lj = lamf[j];
             rk += (lj > li) || (lj == li && j < tid);
         }
         order[rk] = tid;
+        const double c = thr * (w_sv ? w_sv[rk] : 1.0) * (1.0 - 1e-3);
+        if ((double)fmaxf(li, 0.f) > c * c) atomicMax(&r_act, rk + 1);
     }
     if (warm)
         for (int k = tid; k < L * L; k += nt) warm[k] = V32[(k / L) * LD32 + (k % L)];
     __syncthreads();
-    if (tid == 0) {
-        int r = 0;
-        for (int j = 0; j < L; ++j) {
-            const double sig = sqrt(fmax(lam32[order[j]], 0.0));
-            const double c = thr * (w_sv ? w_sv[j] : 1.0);
-            if (sig > c * (1.0 - 1e-3)) r = j + 1;
-        }
-        r_act = r;
-        if (r_out) *r_out = r;
-    }
-    __syncthreads();
+    if (tid == 0 && r_out) *r_out = r_act;
     const int r = r_act;
     if (r > 0) {
         // active vectors in FP64
@@ -271,8 +282,10 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
             X[i * MAX_L_NUC + c] = (double)V32[i * LD32 + order[c]];
         }
         __syncthreads();
-        // ---- 2. two FP64 correction steps of the active vectors against the whole basis
-        for (int step = 0; step < 2; ++step) {
+        // ---- 2. FP64 correction steps of the active vectors against the whole basis
+        // (the first-order step squares the FP32 error: one suffices from a warm basis)
+        const int nsteps = warm ? 1 : 2;
+        for (int step = 0; step < nsteps; ++step) {
             // Y = S X
             for (int k = tid; k < L * r; k += nt) {
                 const int i = k / r, c = k - i * r;
@@ -336,27 +349,43 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
             }
             __syncthreads();
         }
-        // ---- 3. modified Gram-Schmidt on the active vectors
-        for (int c = 0; c < r; ++c) {
-            for (int j = 0; j < c; ++j) {
-                double d = 0.0;
-                for (int m = tid; m < L; m += nt) d += X[m * MAX_L_NUC + j] * X[m * MAX_L_NUC + c];
-                d = eig_bsum(d, red);
-                if (tid == 0) red[31] = d;
-                __syncthreads();
-                d = red[31];
-                for (int m = tid; m < L; m += nt) X[m * MAX_L_NUC + c] -= d * X[m * MAX_L_NUC + j];
-                __syncthreads();
+        // ---- 3. orthonormalise the active vectors (Cholesky QR: G = X^T X = R^T R,
+        //      X <- X R^{-1}; X is orthonormal to first order already, so G ~ I)
+        for (int k = tid; k < r * r; k += nt) {
+            const int a = k / r, b = k - a * r;
+            if (a <= b) {
+                double acc = 0.0;
+                for (int m = 0; m < L; ++m) acc = fma(X[m * MAX_L_NUC + a], X[m * MAX_L_NUC + b], acc);
+                Tb[a * LD32 + b] = acc;
             }
-            double nn = 0.0;
-            for (int m = tid; m < L; m += nt) nn += X[m * MAX_L_NUC + c] * X[m * MAX_L_NUC + c];
-            nn = eig_bsum(nn, red);
-            if (tid == 0) red[31] = nn;
-            __syncthreads();
-            const double inv = 1.0 / sqrt(red[31]);
-            for (int m = tid; m < L; m += nt) X[m * MAX_L_NUC + c] *= inv;
-            __syncthreads();
         }
+        __syncthreads();
+        if (tid < 32) {   // upper-triangular R in place of G, one warp, lanes over columns
+            for (int j = 0; j < r; ++j) {
+                if (tid == 0) {
+                    double d = Tb[j * LD32 + j];
+                    for (int k = 0; k < j; ++k) d -= Tb[k * LD32 + j] * Tb[k * LD32 + j];
+                    Tb[j * LD32 + j] = sqrt(fmax(d, 1e-300));
+                }
+                __syncwarp();
+                const double rjj = Tb[j * LD32 + j];
+                for (int i = j + 1 + tid; i < r; i += 32) {
+                    double v = Tb[j * LD32 + i];
+                    for (int k = 0; k < j; ++k) v -= Tb[k * LD32 + j] * Tb[k * LD32 + i];
+                    Tb[j * LD32 + i] = v / rjj;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int m = tid; m < L; m += nt) {   // row m of X times R^{-1} (forward substitution)
+            for (int j = 0; j < r; ++j) {
+                double v = X[m * MAX_L_NUC + j];
+                for (int k = 0; k < j; ++k) v -= X[m * MAX_L_NUC + k] * Tb[k * LD32 + j];
+                X[m * MAX_L_NUC + j] = v / Tb[j * LD32 + j];
+            }
+        }
+        __syncthreads();
         //      Rayleigh-Ritz: Tr = X^T S X (r x r), FP64 Jacobi, X <- X W
         int nr = 2;
         while (nr < r) nr <<= 1;
@@ -423,10 +452,19 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
         Mf[LR_R] = (double)r;
         Mf[LR_BASE] = dual ? 1.0 : 0.0;
     }
-    if (tid < r) Mf[LR_G + tid] = dual ? lamr[tid] - 1.0 : lamr[tid];
+    float* Ff = reinterpret_cast<float*>(Mf + LR_DOUBLES);   // FP32 copies for the apply kernel
+    if (tid < r) {
+        const double g = dual ? lamr[tid] - 1.0 : lamr[tid];
+        Mf[LR_G + tid] = g;
+        Ff[LRF_G + tid] = (float)g;
+    }
     for (int k = tid; k < L * r; k += nt) {
         const int i = k / r, c = k - i * r;
-        Mf[LR_X + c * MAX_L_NUC + i] = Y[i * MAX_L_NUC + c];
+        const double x = Y[i * MAX_L_NUC + c];
+        const float xh = (float)x;
+        Mf[LR_X + c * MAX_L_NUC + i] = x;
+        Ff[LRF_XH + c * MAX_L_NUC + i] = xh;
+        Ff[LRF_XL + c * MAX_L_NUC + i] = (float)(x - (double)xh);
     }
 }
 

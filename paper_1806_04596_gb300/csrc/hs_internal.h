@@ -46,8 +46,13 @@ constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
 // Low-rank form of the nuclear prox factor M = base I + sum_c g_c x_c x_c^T
 // (doubles in Plan::eigf): [LR_R] active count r, [LR_BASE] 1 (dual) or 0,
 // [LR_G + c] g_c, [LR_X + c * MAX_L_NUC + i] component i of x_c.
+// Followed by FP32 copies for FP32 plans, as floats from double offset LR_DOUBLES:
+// [LRF_XH + c * MAX_L_NUC + i] hi part of x_ci, [LRF_XL + ...] lo part
+// (x = hi + lo to FP64 rounding), [LRF_G + c] g_c.
 constexpr int LR_R = 0, LR_BASE = 1, LR_G = 2, LR_X = 2 + MAX_L_NUC;
 constexpr int LR_DOUBLES = LR_X + MAX_L_NUC * MAX_L_NUC;
+constexpr int LRF_XH = 0, LRF_XL = MAX_L_NUC * MAX_L_NUC, LRF_G = 2 * MAX_L_NUC * MAX_L_NUC;
+constexpr int LR_TOTAL_DOUBLES = LR_DOUBLES + (LRF_G + MAX_L_NUC + 1) / 2;
 
 // Coordinates of one visibility in an FP64 plan: window start cells and the
 // fractional part of t = u K / (2 pi) (exact in FP64).
@@ -105,7 +110,7 @@ struct Plan {
     double* part = nullptr;            // partial sums (size part_n doubles)
     int64_t part_n = 0;
     double* gram = nullptr;            // MAX_L_NUC^2 doubles
-    double* eigf = nullptr;            // LR_DOUBLES: low-rank prox factor (layout above)
+    double* eigf = nullptr;            // LR_TOTAL_DOUBLES: low-rank prox factor (layout above)
     double* sv = nullptr;              // MAX_L_NUC doubles
     double* dscal = nullptr;           // small per-channel doubles (4 * L)
     void* xbuf = nullptr;              // L * N reals (power iteration, misc)

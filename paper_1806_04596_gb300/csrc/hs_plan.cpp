@@ -361,7 +361,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
                                    gram_part_doubles(std::min(L, MAX_L_NUC)), 8192});
     HS_TRY(plan_alloc(p, (void**)&p->part, (size_t)p->part_n * sizeof(double)));
     HS_TRY(plan_alloc(p, (void**)&p->gram, sizeof(double) * MAX_L_NUC * MAX_L_NUC));
-    HS_TRY(plan_alloc(p, (void**)&p->eigf, sizeof(double) * LR_DOUBLES));
+    HS_TRY(plan_alloc(p, (void**)&p->eigf, sizeof(double) * LR_TOTAL_DOUBLES));
     HS_TRY(plan_alloc(p, (void**)&p->sv, sizeof(double) * MAX_L_NUC));
     HS_TRY(plan_alloc(p, (void**)&p->dscal, sizeof(double) * 6 * std::max(L, 1)));
     return HS_OK;

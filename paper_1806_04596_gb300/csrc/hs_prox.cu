@@ -276,19 +276,31 @@ __global__ void __launch_bounds__(256) k_gram(const R* __restrict__ X, const R* 
         lo[q] = 0;
     }
     const int64_t ntile = N / GRAM_PIX;   // N is a multiple of 64 (nx, ny >= 16, powers of two)
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t n0 = tile * GRAM_PIX;
-        __syncthreads();
-        for (int k = tid; k < MAX_L_NUC * GRAM_PIX; k += 256) {
-            const int l = k >> 6, px = k & (GRAM_PIX - 1);
+    // thread tid stages channels (tid >> 6) + 4 m, m < 16, of pixel tid & 63; the
+    // next tile's values are loaded into registers while the current one is used
+    constexpr int PER = MAX_L_NUC * GRAM_PIX / 256;
+    const int px0 = tid & (GRAM_PIX - 1), l0 = tid >> 6;
+    R pre[PER];
+    auto fetch = [&](int64_t tile) {
+        const int64_t n = tile * GRAM_PIX + px0;
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+            const int l = l0 + 4 * m;
             R z = 0;
-            if (l < L) {
-                z = X[(int64_t)l * N + n0 + px];
-                if (Xa) z += Xa[(int64_t)l * N + n0 + px];
+            if (l < L && tile < ntile) {
+                z = X[(int64_t)l * N + n];
+                if (Xa) z += Xa[(int64_t)l * N + n];
             }
-            zs[px][l] = z;
+            pre[m] = z;
         }
+    };
+    fetch(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         __syncthreads();
+#pragma unroll
+        for (int m = 0; m < PER; ++m) zs[px0][l0 + 4 * m] = pre[m];
+        __syncthreads();
+        fetch(tile + gridDim.x);
 #pragma unroll
         for (int half = 0; half < GRAM_PIX / 32; ++half) {
             R acc[16];
@@ -347,33 +359,27 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int L, do
 
 // out[:, n] = M z_n with z = X (+ Xa) and M = base I + sum_{c < r} g_c x_c x_c^T
 // (low-rank form written by the eigensolver): per pixel, r projections
-// p_c = x_c . z and the update out = base z + sum_c (g_c p_c) x_c, the pixel's
-// L values in registers and x_c broadcast from shared memory. In FP32 the FP64
-// vectors are carried as two FP32 parts (hi + lo), so that their rounding does
-// not enter the result: the output is often a small remainder of a large z
-// (the dual form keeps the small singular values).
+// q_c = g_c (x_c . z), then out = base z + sum_c q_c x_c, the pixel's L values
+// in registers (overwritten in place by the output), q_c in shared memory, x_c
+// read with uniform (broadcast) loads. In FP32 the FP64 vectors are carried as
+// two FP32 parts (hi + lo), so that their rounding does not enter the result:
+// the output is often a small remainder of a large z (the dual form keeps the
+// small singular values).
+constexpr int LR_BS = 128;   // pixels (threads) per CTA
+
 template <typename R, int LMAX>
-__global__ void __launch_bounds__(128) k_lowrank_apply(const R* __restrict__ X,
-                                                       const R* __restrict__ Xa,
-                                                       const double* __restrict__ F, int L,
-                                                       int64_t N, R* __restrict__ out) {
+__global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X, const R* __restrict__ Xa,
+                                                         const double* __restrict__ F, int L, int64_t N,
+                                                         R* __restrict__ out) {
     constexpr bool SPLIT = sizeof(R) == 4;
-    __shared__ R xh[LMAX * LMAX];
-    __shared__ R xl[SPLIT ? LMAX * LMAX : 1];
-    __shared__ R gs[LMAX];
+    __shared__ R qs[LMAX * LR_BS];
     const int r = (int)F[LR_R];
     const bool base = F[LR_BASE] != 0.0;
-    for (int k = threadIdx.x; k < r * L; k += blockDim.x) {
-        const int c = k / L, i = k - c * L;
-        const double v = F[LR_X + c * MAX_L_NUC + i];
-        xh[c * LMAX + i] = (R)v;
-        if (SPLIT) xl[c * LMAX + i] = (R)(v - (double)(R)v);
-    }
-    if (threadIdx.x < r) gs[threadIdx.x] = (R)F[LR_G + threadIdx.x];
-    __syncthreads();
-    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float* Ff = reinterpret_cast<const float*>(F + LR_DOUBLES);
+    const int t = threadIdx.x;
+    const int64_t n = blockIdx.x * (int64_t)LR_BS + t;
     if (n >= N) return;
-    R z[LMAX], o[LMAX];
+    R z[LMAX];
 #pragma unroll
     for (int i = 0; i < LMAX; ++i) {
         z[i] = 0;
@@ -381,44 +387,54 @@ __global__ void __launch_bounds__(128) k_lowrank_apply(const R* __restrict__ X,
             z[i] = X[(int64_t)i * N + n];
             if (Xa) z[i] += Xa[(int64_t)i * N + n];
         }
-        o[i] = base ? z[i] : (R)0;
     }
     for (int c = 0; c < r; ++c) {
-        const R* h = xh + c * LMAX;
-        const R* lo = xl + (SPLIT ? c * LMAX : 0);
         R p = 0, p2 = 0;
 #pragma unroll
         for (int i = 0; i < LMAX; ++i)
             if (i < L) {
-                p = fma(z[i], h[i], p);
-                if (SPLIT) p2 = fma(z[i], lo[i], p2);
+                if (SPLIT) {
+                    p = fma(z[i], (R)Ff[LRF_XH + c * MAX_L_NUC + i], p);
+                    p2 = fma(z[i], (R)Ff[LRF_XL + c * MAX_L_NUC + i], p2);
+                } else {
+                    p = fma(z[i], (R)F[LR_X + c * MAX_L_NUC + i], p);
+                }
             }
-        const R q = gs[c] * (p + p2);
+        qs[c * LR_BS + t] = (SPLIT ? (R)Ff[LRF_G + c] : (R)F[LR_G + c]) * (p + p2);
+    }
+    if (!base)
+#pragma unroll
+        for (int i = 0; i < LMAX; ++i) z[i] = 0;
+    for (int c = 0; c < r; ++c) {
+        const R q = qs[c * LR_BS + t];
 #pragma unroll
         for (int i = 0; i < LMAX; ++i)
             if (i < L) {
-                o[i] = fma(q, h[i], o[i]);
-                if (SPLIT) o[i] = fma(q, lo[i], o[i]);
+                if (SPLIT) {
+                    z[i] = fma(q, (R)Ff[LRF_XH + c * MAX_L_NUC + i], z[i]);
+                    z[i] = fma(q, (R)Ff[LRF_XL + c * MAX_L_NUC + i], z[i]);
+                } else {
+                    z[i] = fma(q, (R)F[LR_X + c * MAX_L_NUC + i], z[i]);
+                }
             }
     }
 #pragma unroll
     for (int i = 0; i < LMAX; ++i)
-        if (i < L) out[(int64_t)i * N + n] = o[i];
+        if (i < L) out[(int64_t)i * N + n] = z[i];
 }
 
 template <typename R>
 static hs_status lowrank_apply_t(Plan* p, const void* X, const void* Xa, void* out, cudaStream_t s) {
     const int L = p->g.L;
     const int64_t N = p->N();
-    const unsigned g = nblk(N, 128);
-    if (L <= 8)
-        k_lowrank_apply<R, 8><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
-    else if (L <= 16)
-        k_lowrank_apply<R, 16><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
-    else if (L <= 32)
-        k_lowrank_apply<R, 32><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
-    else
-        k_lowrank_apply<R, 64><<<g, 128, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out);
+    const unsigned g = nblk(N, LR_BS);
+#define HS_LR(LM) \
+    k_lowrank_apply<R, LM><<<g, LR_BS, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out)
+    if (L <= 8) HS_LR(8);
+    else if (L <= 16) HS_LR(16);
+    else if (L <= 32) HS_LR(32);
+    else HS_LR(64);
+#undef HS_LR
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
