@@ -13,15 +13,14 @@
 //  2. The active eigenvectors are refined in FP64 against the rest of the
 //     basis with first-order correction steps (one from a warm basis, two
 //     cold) of an approximate eigendecomposition (Ogita & Aishima 2018): with
-//     b_j the basis, T = B^T S X,
-//     R = I - B^T X, lambda_c = T_cc / (1 - R_cc), the correction of x_c along
-//     b_j is (T_jc + lambda_c R_jc) / (lambda_c - lambda_j) across the active /
-//     inactive boundary and R_jc / 2 (orthogonalisation only) inside the active
-//     set or for near-equal eigenvalues (those straddle the threshold, where f
-//     is continuous, so their mixing does not change the result).
-//  3. Cholesky QR, then an FP64 Rayleigh-Ritz step on the active
-//     subspace (FP64 Jacobi on the r x r matrix X^T S X) resolves the
-//     eigenpairs inside it.
+//     b_j the basis (the active vectors themselves, then the inactive FP32
+//     eigenvectors), T = B^T S X, R = I - B^T X, lambda_c = T_cc / (1 - R_cc),
+//     the correction of x_c along b_j (j != c) is
+//     (T_jc + lambda_c R_jc) / (lambda_c - lambda_j), and R_jc / 2
+//     (orthogonalisation only) along x_c itself or for near-equal eigenvalues
+//     (their mixing leaves f, continuous in sigma, unchanged to first order).
+//     The eigenvalues are the last step's Rayleigh quotients lambda_c.
+//  3. Cholesky QR keeps the active vectors orthonormal in FP64.
 //  4. The factor is returned in low-rank form: M = I - sum_active (1 - f) x x^T
 //     (dual) or sum_active f x x^T (prox), as r, g and the active x.
 #include <cmath>
@@ -39,9 +38,9 @@ __device__ __forceinline__ double eig_bsum(double v, double* red) { return block
 
 // Round-robin (circle method) schedule for n indices, n even: in round r the
 // index n-1 meets r and (r + i) meets (r - i) (mod n-1) for i = 1 .. n/2-1.
-// pairs[r * n + 2 k], pairs[r * n + 2 k + 1] = (p, q), p < q, is the k-th
-// pair of round r (thread r lists its round).
-__device__ void rr_schedule(int n, unsigned char* pairs) {
+// pairs[r * n/2 + k] = p | q << 8 (p < q) is the k-th pair of round r (thread r
+// lists its round).
+__device__ void rr_schedule(int n, unsigned short* pairs) {
     for (int r = threadIdx.x; r < n - 1; r += blockDim.x) {
         int k = 0;
         for (int i = 0; i < n; ++i) {
@@ -49,11 +48,7 @@ __device__ void rr_schedule(int n, unsigned char* pairs) {
             if (i == n - 1) pi = r;
             else if (i == r) pi = n - 1;
             else pi = ((2 * r - i) % (n - 1) + (n - 1)) % (n - 1);
-            if (i < pi) {
-                pairs[r * n + 2 * k] = (unsigned char)i;
-                pairs[r * n + 2 * k + 1] = (unsigned char)pi;
-                ++k;
-            }
+            if (i < pi) pairs[r * (n / 2) + k++] = (unsigned short)(i | (pi << 8));
         }
     }
 }
@@ -76,25 +71,26 @@ __device__ __forceinline__ void jac_rot(double app, double aqq, double apq, doub
 
 // Cyclic Jacobi, round-robin parallel ordering, on the symmetric N x N matrix
 // in A (leading dimension LDJ), accumulating V <- V J. Each round, thread k < N/2
-// computes the rotation of pair k = (p, q) from a_pp, a_qq, a_pq (symmetric
-// Schur decomposition, Golub & Van Loan Alg. 8.4.1: J_pp = J_qq = c,
-// J_pq = s, J_qp = -s); then thread (i, j) of the (N/2)^2 block grid applies
-// A <- J^T A J to the 2 x 2 block (rows of pair i, columns of pair j):
+// computes the rotation (c_k, s_k) of pair k = (p, q) from a_pp, a_qq, a_pq
+// (J_pp = J_qq = c, J_pq = s, J_qp = -s); then thread (i, j) of the (N/2)^2
+// grid applies A <- J^T A J to the 2 x 2 block (rows of pair i, columns of
+// pair j):
 //   rows   (p, q) <- (c_i row_p - s_i row_q, s_i row_p + c_i row_q)
 //   cols   (p, q) <- (c_j col_p - s_j col_q, s_j col_p + c_j col_q),
-// and the columns of V are rotated the same way. Every entry belongs to one
-// thread per round, so A and V are updated in place (4 loads and 4 stores per
-// block). A rotation is applied only when |a_pq| exceeds skip sqrt(|a_pp a_qq|)
-// and floor_rel ||A||_F; sweeps stop when the off-diagonal Frobenius norm is at
-// most off_rel ||A||_F, when a sweep applies no rotation, or after max_sweeps.
+// and rotates columns (p_j, q_j) of V in rows i and i + N/2. Every entry belongs
+// to one thread per round, so A and V are updated in place. A rotation is
+// applied only when |a_pq| exceeds skip sqrt(|a_pp a_qq|) and floor_rel ||A||_F;
+// sweeps stop when the off-diagonal Frobenius norm is at most off_rel ||A||_F,
+// when a sweep applies no rotation, or after max_sweeps.
 template <typename T, int N>
-__device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double skip, double floor_rel,
-                              double off_rel, int max_sweeps, T* cvec, T* svec, double* red, int* flag) {
+__device__ void jacobi_blocks(T* A, T* V, const unsigned short* pairs, double skip, double floor_rel,
+                              double off_rel, int max_sweeps, Cx<T>* cs, double* red, int* flag) {
     constexpr int LDJ = MAX_L_NUC + 1;
     constexpr int NP = N / 2;
     constexpr int LG = (N >= 64) ? 6 : (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     const T skip2 = (T)(skip * skip);
+    const int bi = tid / NP, bj = tid - (tid / NP) * NP;   // block of this thread (tid < NP^2)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         T nrmT = 0, offT = 0;   // per-thread partial sums in the working precision
         for (int k = tid; k < N * N; k += nt) {
@@ -110,9 +106,9 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
         if (tid == 0) *flag = 0;
         __syncthreads();
         for (int r = 0; r < N - 1; ++r) {
-            const unsigned char* pr = pairs + r * N;
+            const unsigned short* pr = pairs + r * NP;
             if (tid < NP) {
-                const int p = pr[2 * tid], q = pr[2 * tid + 1];
+                const int pq = pr[tid], p = pq & 0xff, q = pq >> 8;
                 const T apq = A[p * LDJ + q], app = A[p * LDJ + p], aqq = A[q * LDJ + q];
                 T c = 1, s = 0;
                 const T ab = fabs(apq);
@@ -120,16 +116,21 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
                     jac_rot(app, aqq, apq, c, s);
                     *flag = 1;
                 }
-                cvec[tid] = c;
-                svec[tid] = s;
+                Cx<T> v;
+                v.x = c;
+                v.y = s;
+                cs[tid] = v;
             }
             __syncthreads();
             if (tid < NP * NP) {
-                const int bi = tid / NP, bj = tid - bi * NP;
-                const int pi = pr[2 * bi], qi = pr[2 * bi + 1], pj = pr[2 * bj], qj = pr[2 * bj + 1];
-                const T ci = cvec[bi], si = svec[bi], cj = cvec[bj], sj = svec[bj];
+                const int pqi = pr[bi], pqj = pr[bj];
+                const int pi = pqi & 0xff, qi = pqi >> 8, pj = pqj & 0xff, qj = pqj >> 8;
+                const Cx<T> csi = cs[bi], csj = cs[bj];
+                const T ci = csi.x, si = csi.y, cj = csj.x, sj = csj.y;
                 const T a00 = A[pi * LDJ + pj], a01 = A[pi * LDJ + qj];
                 const T a10 = A[qi * LDJ + pj], a11 = A[qi * LDJ + qj];
+                const T v00 = V[bi * LDJ + pj], v01 = V[bi * LDJ + qj];
+                const T v10 = V[(bi + NP) * LDJ + pj], v11 = V[(bi + NP) * LDJ + qj];
                 const T r0x = ci * a00 - si * a10, r0y = ci * a01 - si * a11;
                 const T r1x = si * a00 + ci * a10, r1y = si * a01 + ci * a11;
                 T b00 = cj * r0x - sj * r0y, b01 = sj * r0x + cj * r0y;
@@ -142,14 +143,10 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
                 A[pi * LDJ + qj] = b01;
                 A[qi * LDJ + pj] = b10;
                 A[qi * LDJ + qj] = b11;
-            }
-            for (int u = tid; u < N * NP; u += nt) {
-                const int k = u / NP, j = u - k * NP;
-                const int p = pr[2 * j], q = pr[2 * j + 1];
-                const T c = cvec[j], s = svec[j];
-                const T v0 = V[k * LDJ + p], v1 = V[k * LDJ + q];
-                V[k * LDJ + p] = c * v0 - s * v1;
-                V[k * LDJ + q] = s * v0 + c * v1;
+                V[bi * LDJ + pj] = cj * v00 - sj * v01;
+                V[bi * LDJ + qj] = sj * v00 + cj * v01;
+                V[(bi + NP) * LDJ + pj] = cj * v10 - sj * v11;
+                V[(bi + NP) * LDJ + qj] = sj * v10 + cj * v11;
             }
             __syncthreads();
         }
@@ -162,15 +159,13 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned char* pairs, double ski
 // Dispatch on the padded size n (power of two, 2..64). B and W are unused
 // scratch kept for the callers' layouts.
 template <typename T>
-__device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, unsigned char* pairs, double skip,
-                         double floor_rel, double off_rel, int max_sweeps, T* cvec, T* tvec,
-                         double* red, int* flag) {
+__device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, unsigned short* pairs, double skip,
+                         double floor_rel, double off_rel, int max_sweeps, Cx<T>* cs, double* red, int* flag) {
     (void)B;
     (void)W;
     rr_schedule(n, pairs);
     __syncthreads();
-#define HS_JAC(NN) \
-    jacobi_blocks<T, NN>(A, V, pairs, skip, floor_rel, off_rel, max_sweeps, cvec, tvec, red, flag)
+#define HS_JAC(NN) jacobi_blocks<T, NN>(A, V, pairs, skip, floor_rel, off_rel, max_sweeps, cs, red, flag)
     switch (n) {
         case 2: HS_JAC(2); break;
         case 4: HS_JAC(4); break;
@@ -199,17 +194,15 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     double* X = Sd + SL;                                 // active vectors (columns)
     double* Y = X + SL;
     double* Rb = Y + SL;
-    // FP64 views over the float slots once those are dead: slots 2-3 and slots 0-1
+    // FP64 view over float slots 2-3 once the FP32 Jacobi matrix is dead
     double* Tb = (double*)A32;
-    double* Ub = (double*)V32;
     __shared__ double red[33];
-    __shared__ float cv32[MAX_L_NUC], tv32[MAX_L_NUC];
-    __shared__ double cv64[MAX_L_NUC], tv64[MAX_L_NUC];
-    __shared__ unsigned char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ float2 cs32[MAX_L_NUC / 2];
+    __shared__ unsigned short partner[(MAX_L_NUC - 1) * MAX_L_NUC / 2];
     __shared__ int flag;
     __shared__ double lam32[MAX_L_NUC], lamr[MAX_L_NUC], fv[MAX_L_NUC];
     __shared__ float lamf[MAX_L_NUC];
-    __shared__ int order[MAX_L_NUC], ordr[MAX_L_NUC];
+    __shared__ int order[MAX_L_NUC];
     __shared__ int r_act;
     const int tid = threadIdx.x, nt = blockDim.x;
     int n = 2;
@@ -251,7 +244,7 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     // ---- 1. FP32 Jacobi on every eigenpair
     // warm-started calls run one FP32 sweep: the active pairs are made exact in
     // FP64 below, and the basis keeps improving from call to call
-    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 1 : 15, cv32, tv32, red, &flag);
+    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 1 : 15, cs32, red, &flag);
     // ---- eigenvalues, descending order (rank by counting), warm start for the next call
     if (tid < L) {
         lamf[tid] = A32[tid * LD32 + tid];
@@ -324,12 +317,8 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
                 const int j = k / r, c = k - j * r;
                 const double t = Tb[j * MAX_L_NUC + c], q = Rb[j * MAX_L_NUC + c];
                 double e;
-                if (j < r) {
-                    e = 0.5 * q;
-                } else {
-                    const double gap = lamr[c] - lam32[order[j]];
-                    e = (fabs(gap) > delta) ? (t + lamr[c] * q) / gap : 0.5 * q;
-                }
+                const double gap = lamr[c] - (j < r ? lamr[j] : lam32[order[j]]);
+                e = (j != c && fabs(gap) > delta) ? (t + lamr[c] * q) / gap : 0.5 * q;
                 Tb[j * MAX_L_NUC + c] = e;
             }
             __syncthreads();
@@ -386,62 +375,15 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
             }
         }
         __syncthreads();
-        //      Rayleigh-Ritz: Tr = X^T S X (r x r), FP64 Jacobi, X <- X W
-        int nr = 2;
-        while (nr < r) nr <<= 1;
-        for (int k = tid; k < L * r; k += nt) {
-            const int i = k / r, c = k - i * r;
-            double acc = 0.0;
-            for (int m = 0; m < L; ++m) acc = fma(Sd[i * MAX_L_NUC + m], X[m * MAX_L_NUC + c], acc);
-            Y[i * MAX_L_NUC + c] = acc;
-        }
-        __syncthreads();
-        for (int k = tid; k < nr * nr; k += nt) {
-            const int a = k / nr, b = k - a * nr;
-            double acc = 0.0;
-            if (a < r && b < r)
-                for (int m = 0; m < L; ++m) acc = fma(X[m * MAX_L_NUC + a], Y[m * MAX_L_NUC + b], acc);
-            Tb[a * LD32 + b] = acc;
-            Rb[a * LD32 + b] = (a == b) ? 1.0 : 0.0;
-        }
-        __syncthreads();
-        for (int k = tid; k < nr * nr; k += nt) {   // symmetrise
-            const int a = k / nr, b = k - a * nr;
-            if (a < b) {
-                const double v = 0.5 * (Tb[a * LD32 + b] + Tb[b * LD32 + a]);
-                Tb[a * LD32 + b] = v;
-                Tb[b * LD32 + a] = v;
-            }
-        }
-        __syncthreads();
-        jacobi_n<double>(nr, Tb, Ub, Rb, Sd, partner, 1e-16, 1e-17, 1e-15, 40, cv64, tv64, red, &flag);
-        if (tid < r) lamr[tid] = Tb[tid * LD32 + tid];
-        __syncthreads();
+        // eigenvalues: the last step's Rayleigh quotients (second-order accurate)
         if (tid < r) {
-            int rk = 0;
-            const double li = lamr[tid];
-            for (int j = 0; j < r; ++j) rk += (lamr[j] > li) || (lamr[j] == li && j < tid);
-            ordr[rk] = tid;
-        }
-        __syncthreads();
-        for (int k = tid; k < L * r; k += nt) {   // Y = X W, columns in descending order
-            const int i = k / r, c = k - i * r;
-            const int src = ordr[c];
-            double acc = 0.0;
-            for (int j = 0; j < r; ++j) acc = fma(X[i * MAX_L_NUC + j], Rb[j * LD32 + src], acc);
-            Y[i * MAX_L_NUC + c] = acc;
-        }
-        __syncthreads();
-        if (tid < r) fv[tid] = lamr[ordr[tid]];
-        __syncthreads();
-        if (tid < r) {
-            const double sig = sqrt(fmax(fv[tid], 0.0));
+            const double sig = sqrt(fmax(lamr[tid], 0.0));
             const double c = thr * (w_sv ? w_sv[tid] : 1.0);
             double f;
             if (dual) f = (sig > c) ? c / sig : 1.0;
             else f = (sig > c) ? 1.0 - c / sig : 0.0;
             if (sv_out) sv_out[tid] = sig;
-            lamr[tid] = f;   // factor of active vector tid (descending)
+            fv[tid] = f;   // factor of active vector tid
         }
         __syncthreads();
     }
@@ -454,13 +396,13 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     }
     float* Ff = reinterpret_cast<float*>(Mf + LR_DOUBLES);   // FP32 copies for the apply kernel
     if (tid < r) {
-        const double g = dual ? lamr[tid] - 1.0 : lamr[tid];
+        const double g = dual ? fv[tid] - 1.0 : fv[tid];
         Mf[LR_G + tid] = g;
         Ff[LRF_G + tid] = (float)g;
     }
     for (int k = tid; k < L * r; k += nt) {
         const int i = k / r, c = k - i * r;
-        const double x = Y[i * MAX_L_NUC + c];
+        const double x = X[i * MAX_L_NUC + c];
         const float xh = (float)x;
         Mf[LR_X + c * MAX_L_NUC + i] = x;
         Ff[LRF_XH + c * MAX_L_NUC + i] = xh;
@@ -485,9 +427,10 @@ __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg
     double* V = B + SL;
     double* W = V + SL;
     __shared__ double red[33];
-    __shared__ double cv[MAX_L_NUC], tv[MAX_L_NUC], lam[MAX_L_NUC], fv[MAX_L_NUC];
+    __shared__ double lam[MAX_L_NUC], fv[MAX_L_NUC];
+    __shared__ double2 cs[MAX_L_NUC / 2];
     __shared__ int order[MAX_L_NUC];
-    __shared__ unsigned char partner[(MAX_L_NUC - 1) * MAX_L_NUC];
+    __shared__ unsigned short partner[(MAX_L_NUC - 1) * MAX_L_NUC / 2];
     __shared__ int flag;
     const int tid = threadIdx.x, nt = blockDim.x;
     int n = 2;
@@ -498,7 +441,7 @@ __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg
         V[i * LD32 + j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    jacobi_n<double>(n, A, B, V, W, partner, 1e-17, 1e-18, 1e-16, 40, cv, tv, red, &flag);
+    jacobi_n<double>(n, A, B, V, W, partner, 1e-17, 1e-18, 1e-16, 40, cs, red, &flag);
     if (tid < L) lam[tid] = A[tid * LD32 + tid];
     __syncthreads();
     if (tid < L) {
