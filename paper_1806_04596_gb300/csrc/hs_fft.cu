@@ -98,24 +98,27 @@ __device__ __forceinline__ void fft_store(const FftArgs<R>& a, int la, int lb, i
 
 // One Stockham pass of radix RAD (LGR = log2 RAD) over the CTA's G lines:
 // every thread owns 8 / RAD butterflies (8 operands, all in registers).
-template <typename R, int DIR, int MODE, int RAD, int LGR>
+// LGK_ / LGG_ > 0 fix log2 K and log2 G at compile time (0: from the arguments).
+template <typename R, int DIR, int MODE, int RAD, int LGR, int LGK_, int LGG_>
 __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgNs, bool first,
                                          bool last, int line0) {
     typedef Cx<R> CT;
     constexpr bool COLS = (MODE == COL_FWD || MODE == COL_INV);
     constexpr int PER = 8 / RAD;
-    const int K = a.K, G = a.G;
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int lgnb = a.lgK - LGR;
+    const int lgK = LGK_ > 0 ? LGK_ : a.lgK;
+    const int lgG = LGG_ > 0 || LGK_ > 0 ? LGG_ : a.lgG;
+    const int K = 1 << lgK, G = 1 << lgG;
+    const int nthr = LGK_ > 0 ? (G << lgK) >> 3 : blockDim.x, tid = threadIdx.x;
+    const int lgnb = lgK - LGR;
     const int nb = 1 << lgnb;
-    const int lgstep = a.lgK - lgNs - LGR;
+    const int lgstep = lgK - lgNs - LGR;
     CT v[8];
     int gs[PER], js[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int w = tid + i * nthr;
         const int g = COLS ? (w & (G - 1)) : (w >> lgnb);
-        const int j = COLS ? (w >> a.lgG) : (w & (nb - 1));
+        const int j = COLS ? (w >> lgG) : (w & (nb - 1));
         gs[i] = g;
         js[i] = j;
         int la = 0, lb = 0;
@@ -163,23 +166,37 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgN
 }
 
 // DIR = -1: forward transform (exp(-2 pi i kn / K)); DIR = +1: unnormalised inverse.
-template <typename R, int DIR, int MODE>
+// LGK_ > 0: K = 2^LGK_ lines of G = 2^LGG_ per CTA fixed at compile time (the
+// pass schedule and every index computation fold to constants); 0: generic.
+template <typename R, int DIR, int MODE, int LGK_, int LGG_>
 __global__ void __launch_bounds__(512, 2) k_fft(FftArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<R>* sm = reinterpret_cast<Cx<R>*>(smem_raw);
-    const int line0 = blockIdx.x * a.G;
-    int lgNs = 0;
-    for (int pass = 0; pass < a.npass; ++pass) {
-        const bool first = (pass == 0), last = (pass == a.npass - 1);
-        if (pass < a.n8) {
-            fft_pass<R, DIR, MODE, 8, 3>(a, sm, lgNs, first, last, line0);
-            lgNs += 3;
-        } else if (a.rlast == 4) {
-            fft_pass<R, DIR, MODE, 4, 2>(a, sm, lgNs, first, last, line0);
-            lgNs += 2;
-        } else {
-            fft_pass<R, DIR, MODE, 2, 1>(a, sm, lgNs, first, last, line0);
-            lgNs += 1;
+    if constexpr (LGK_ > 0) {
+        constexpr int N8 = LGK_ / 3, REM = LGK_ % 3, NPASS = N8 + (REM ? 1 : 0);
+        const int line0 = blockIdx.x << LGG_;
+#pragma unroll
+        for (int pass = 0; pass < NPASS; ++pass) {
+            const bool first = (pass == 0), last = (pass == NPASS - 1);
+            if (pass < N8) fft_pass<R, DIR, MODE, 8, 3, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
+            else if (REM == 2) fft_pass<R, DIR, MODE, 4, 2, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
+            else fft_pass<R, DIR, MODE, 2, 1, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
+        }
+    } else {
+        const int line0 = blockIdx.x * a.G;
+        int lgNs = 0;
+        for (int pass = 0; pass < a.npass; ++pass) {
+            const bool first = (pass == 0), last = (pass == a.npass - 1);
+            if (pass < a.n8) {
+                fft_pass<R, DIR, MODE, 8, 3, 0, 0>(a, sm, lgNs, first, last, line0);
+                lgNs += 3;
+            } else if (a.rlast == 4) {
+                fft_pass<R, DIR, MODE, 4, 2, 0, 0>(a, sm, lgNs, first, last, line0);
+                lgNs += 2;
+            } else {
+                fft_pass<R, DIR, MODE, 2, 1, 0, 0>(a, sm, lgNs, first, last, line0);
+                lgNs += 1;
+            }
         }
     }
 }
@@ -204,7 +221,7 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
     a.Ky = p->g.Ky;
     a.cxs = (const R*)p->cxs;
     a.cys = (const R*)p->cys;
-    const bool cols = (MODE == COL_FWD || MODE == COL_INV);
+    constexpr bool cols = (MODE == COL_FWD || MODE == COL_INV);
     const int K = cols ? p->g.Ky : p->g.Kx;
     a.K = K;
     a.tw = (const Cx<R>*)(cols ? p->twy : p->twx);
@@ -237,14 +254,43 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
     const size_t smem = (size_t)G * K * sizeof(Cx<R>);
     const int blocks = nlines / G;
     if (blocks == 0) return HS_OK;
-    k_fft<R, DIR, MODE><<<blocks, threads, smem, s>>>(a);
+    // compile-time sizes for the common grids (G as chosen above for these K)
+#define HS_FFT_CT(LK, LG) \
+    if (a.lgK == LK && a.lgG == LG) { \
+        k_fft<R, DIR, MODE, LK, LG><<<blocks, threads, smem, s>>>(a); \
+        HS_CHECK_LAUNCH(); \
+        return HS_OK; \
+    }
+    if constexpr (cols) {
+        HS_FFT_CT(9, 3)
+        HS_FFT_CT(10, 2)
+        HS_FFT_CT(11, 1)
+        HS_FFT_CT(12, 0)
+    } else {
+        HS_FFT_CT(9, 2)
+        HS_FFT_CT(10, 1)
+        HS_FFT_CT(11, 0)
+        HS_FFT_CT(12, 0)
+    }
+#undef HS_FFT_CT
+    k_fft<R, DIR, MODE, 0, 0><<<blocks, threads, smem, s>>>(a);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
 
-template <typename R, int DIR, int MODE> static hs_status fft_attr() {
-    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft<R, DIR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename R, int DIR, int MODE, int LK, int LG> static hs_status fft_attr1() {
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft<R, DIR, MODE, LK, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
+    return HS_OK;
+}
+
+template <typename R, int DIR, int MODE> static hs_status fft_attr() {
+    constexpr bool cols = (MODE == COL_FWD || MODE == COL_INV);
+    HS_TRY((fft_attr1<R, DIR, MODE, 0, 0>()));
+    HS_TRY((fft_attr1<R, DIR, MODE, 9, cols ? 3 : 2>()));
+    HS_TRY((fft_attr1<R, DIR, MODE, 10, cols ? 2 : 1>()));
+    HS_TRY((fft_attr1<R, DIR, MODE, 11, cols ? 1 : 0>()));
+    HS_TRY((fft_attr1<R, DIR, MODE, 12, 0>()));
     return HS_OK;
 }
 

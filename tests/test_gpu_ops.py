@@ -18,6 +18,11 @@ CASES = {
     "ragged64": dict(n=64, L=4, M=(2000, 1503, 0, 911), seed=11),
     "rect": dict(nx=64, ny=32, L=3, M=(700, 333, 1200), seed=12),
     "wide_uv": dict(n=32, L=2, M=(900, 1000), seed=13, uv_std=1.4),
+    # large grids: every compile-time FFT size (K = 1024 rows and columns; K = 2048 and 4096
+    # along either axis)
+    "big512": dict(n=512, L=2, M=(500, 300), seed=14),
+    "big_rect_x": dict(nx=2048, ny=1024, L=1, M=(400,), seed=15),
+    "big_rect_y": dict(nx=1024, ny=2048, L=1, M=(400,), seed=16),
 }
 
 
