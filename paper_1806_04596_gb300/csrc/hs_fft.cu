@@ -136,11 +136,30 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgN
         const int j = js[i];
         const int kk = j & ((1 << lgNs) - 1);
         CT* u = v + i * RAD;
+        if (lgNs > 0) {   // the first pass has unit twiddles
+            if (RAD == 8) {
+                // w^1, w^2, w^4 from the table, the others as products (one rounding each)
+                CT t[8];
+                t[1] = a.tw[kk << lgstep];
+                t[2] = a.tw[(2 * kk) << lgstep];
+                t[4] = a.tw[(4 * kk) << lgstep];
+                t[3] = cmul(t[1], t[2]);
+                t[5] = cmul(t[1], t[4]);
+                t[6] = cmul(t[2], t[4]);
+                t[7] = cmul(t[3], t[4]);
 #pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-            CT t = a.tw[(kk * r) << lgstep];
-            if (DIR > 0) t.y = -t.y;
-            u[r] = cmul(u[r], t);
+                for (int r = 1; r < 8; ++r) {
+                    if (DIR > 0) t[r].y = -t[r].y;
+                    u[r] = cmul(u[r], t[r]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) {
+                    CT t = a.tw[(kk * r) << lgstep];
+                    if (DIR > 0) t.y = -t.y;
+                    u[r] = cmul(u[r], t);
+                }
+            }
         }
         if (RAD == 8) {
             dft8<R, DIR>(u);
