@@ -41,7 +41,7 @@ struct hs_pd_state {
     void* scale = nullptr;  // L reals
     double* beta = nullptr; // 1
     double* ppart = nullptr;   // primal partial sums
-    double* dpart = nullptr;   // de-gridding partial sums
+    double* dpart = nullptr;   // de-gridding partial sums [L][nbx] (one slot per work item)
     float* warm = nullptr;     // L x L eigenvectors of the previous nuclear step (FP32 plans)
     double* sv = nullptr;      // L singular values of the last nuclear step
     int* nact = nullptr;       // active count of the last nuclear step
@@ -441,7 +441,7 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     ALLOC(st->beta, sizeof(double));
     st->nprim = 1024;
     ALLOC(st->ppart, 2 * st->nprim * sizeof(double));
-    st->nbx = std::max(1, degrid_blocks_x(p));
+    st->nbx = degrid_items_max(p);   // slots l * nbx + k; slots without a work item stay 0
     ALLOC(st->dpart, (size_t)L * st->nbx * sizeof(double));
     ALLOC(st->warm, (size_t)MAX_L_NUC * MAX_L_NUC * sizeof(float));
     ALLOC(st->sv, (size_t)std::max(L, 1) * sizeof(double));
@@ -462,6 +462,7 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     HS_TRY(cu(cudaMemsetAsync(st->rho, 0, L * sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->sv, 0, L * sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->nact, 0, sizeof(int), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->dpart, 0, (size_t)L * st->nbx * sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemcpyAsync(st->eps, eps, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "eps"));
     if (L <= MAX_L_NUC) {   // warm start of the eigensolver: identity
         std::vector<float> eye((size_t)L * L, 0.f);

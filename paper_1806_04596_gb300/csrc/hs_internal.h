@@ -88,6 +88,9 @@ struct Plan {
     void* u_sorted = nullptr;          // U in sorted order (real) or null
     int64_t n_ent = 0;
     int64_t* tile_off = nullptr;       // L * ntiles + 1
+    void* dg_items = nullptr;          // de-gridding work items {tix, e0, e1, slot}
+    int64_t n_dg_items = 0;
+    int dg_items_max = 0;              // most items of one channel (partial-sum stride)
     int* tile_ent = nullptr;           // per (channel, tile): groups of 4 sorted visibility indices
                                        // with non-overlapping windows, -1 = padding
     void* grid_items = nullptr;        // gridding work items {tix, e0, e1, slot}
@@ -154,7 +157,8 @@ struct DegridArgs {
     double* part;           // DOUT_PD: per-CTA partial ||d||^2, [L][blocks_x]
 };
 hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s);
-int degrid_blocks_x(const Plan* p);
+int degrid_blocks_x(const Plan* p);   // chunks of DEGRID_CHUNK per channel (l2-ball partials)
+int degrid_items_max(const Plan* p);  // partial-sum stride of the PD de-gridding (>= 1)
 
 struct GridArgs {
     int mode;

@@ -74,18 +74,45 @@ template <typename R> struct NufftK {
 };
 
 // ---------------------------------------------------------------- de-gridding
+// Work item (built by the plan): a run of at most DEGRID_CHUNK sorted
+// visibilities of one channel whose windows start in one 32 x 32 tile. The CTA
+// stages the tile's (32 + 8) x (32 + 8) window region of the grid into shared
+// memory with asynchronous copies (one global read per cell, wrapped), then
+// interpolates every visibility from shared memory.
+struct DgItem {
+    int tix;      // l * ntiles + tile
+    int e0, e1;   // sorted visibility range
+    int slot;     // partial-sum slot (PD mode)
+};
+constexpr int DG_REG = GRID_TILE + 8;   // staged region side (window start offsets 0..32)
+constexpr int DG_LDS = DG_REG + 1;
+
+template <typename R> __device__ __forceinline__ void cp_async_cx(Cx<R>* dst, const Cx<R>* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
+__global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __restrict__ items) {
     typedef Cx<R> CT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CT* S = reinterpret_cast<CT*>(smem_raw);   // [DG_REG][DG_LDS]
     __shared__ double red[32];
-    const int l = blockIdx.y;
-    const int64_t cbeg = a.off[l], cend = a.off[l + 1];
-    const int64_t beg = cbeg + (int64_t)blockIdx.x * DEGRID_CHUNK;
-    const int64_t end = min(cend, beg + DEGRID_CHUNK);
-    if (beg >= end) {
-        if (MODE == DOUT_PD && threadIdx.x == 0) a.part[(int64_t)l * a.nblk_x + blockIdx.x] = 0.0;
-        return;
+    const DgItem it = items[blockIdx.x];
+    const int ntiles = a.g.ntx * a.g.nty;
+    const int l = it.tix / ntiles;
+    const int t = it.tix - l * ntiles;
+    const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int ty0 = (t / a.g.ntx) * a.g.ty, tx0 = (t % a.g.ntx) * a.g.tx;
+    const CT* G = a.grid + (int64_t)l * Ky * Kx;
+    for (int k = threadIdx.x; k < DG_REG * DG_REG; k += blockDim.x) {
+        const int r = k / DG_REG, c = k - r * DG_REG;
+        cp_async_cx<R>(S + r * DG_LDS + c, G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1)));
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int j = lane & 7;              // window column / tap owned by this lane
     const int grp = threadIdx.x >> 3;    // 32 groups of 8 lanes
@@ -93,30 +120,33 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
     R c[NC];
 #pragma unroll
     for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - j) * NC + k];
-    const int Kx = a.g.Kx, Ky = a.g.Ky;
-    const CT* G = a.grid + (int64_t)l * Ky * Kx;
+    const int64_t beg = it.e0, end = it.e1;
     R sq = 0;   // this thread's share of ||d||^2 (few terms; FP64 only for the block sum)
-    // lane j of a group preloads the coordinates of the group's j-th visibility,
-    // so the 8 coordinate loads of a group are in flight together
+    // lane j of a group preloads the coordinates of the group's j-th visibility
     int pcx = 0, pcy = 0;
     R pfx = 0, pfy = 0;
     {
         const int64_t ip = beg + grp + 32 * j;
         if (ip < end) VisCoord<R>::get(a.coords, ip, a.g, pcx, pcy, pfx, pfy);
     }
-    // two visibilities per group and step: their 16 grid loads are issued together
-    for (int it = 0; it < DEGRID_CHUNK / 32; it += 2) {
-        int col[2], k0y[2];
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    // two visibilities per group and step
+    for (int it2 = 0; it2 < DEGRID_CHUNK / 32; it2 += 2) {
+        if (beg + 32 * it2 >= end) break;   // uniform over the CTA
+        int off[2];
         R pu[2], pv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int src = gbase + it + h;
+            const int src = gbase + it2 + h;
             const int cxv = __shfl_sync(0xffffffffu, pcx, src);
             const int cyv = __shfl_sync(0xffffffffu, pcy, src);
             const R fx = __shfl_sync(0xffffffffu, pfx, src);
             const R fy = __shfl_sync(0xffffffffu, pfy, src);
-            col[h] = (((cxv - 3) & (Kx - 1)) + j) & (Kx - 1);
-            k0y[h] = (cyv - 3) & (Ky - 1);
+            // window start relative to the staged region: 0..32 (carry included)
+            const int ox = (((cxv - 3) & (Kx - 1)) - tx0) & (Kx - 1);
+            const int oy = (((cyv - 3) & (Ky - 1)) - ty0) & (Ky - 1);
+            off[h] = min(oy, DG_REG - 8) * DG_LDS + min(ox, DG_REG - 8) + j;
             pu[h] = horner<R, NC>(c, (R)2 * fx - (R)1);
             pv[h] = horner<R, NC>(c, (R)2 * fy - (R)1);
         }
@@ -124,7 +154,7 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int r = 0; r < 8; ++r) gv[h][r] = G[(int64_t)((k0y[h] + r) & (Ky - 1)) * Kx + col[h]];
+            for (int r = 0; r < 8; ++r) gv[h][r] = S[off[h] + r * DG_LDS];
         CT acc[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -147,7 +177,7 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
             }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int64_t i = beg + grp + 32 * (it + h);
+            const int64_t i = beg + grp + 32 * (it2 + h);
             if (i >= end || j != 0) continue;
             CT v = acc[h];
             if (a.w) v = cscale(v, a.w[i]);
@@ -176,7 +206,7 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a) {
     }
     if (MODE == DOUT_PD) {
         const double tot = block_sum((double)sq, red);
-        if (threadIdx.x == 0) a.part[(int64_t)l * a.nblk_x + blockIdx.x] = tot;
+        if (threadIdx.x == 0) a.part[it.slot] = tot;
     }
 }
 
@@ -478,6 +508,7 @@ __global__ void k_grid_merge(const GridMerge* __restrict__ merges, const Cx<R>* 
 
 // ---------------------------------------------------------------- launches
 int degrid_blocks_x(const Plan* p) { return (p->Mmax + DEGRID_CHUNK - 1) / DEGRID_CHUNK; }
+int degrid_items_max(const Plan* p) { return p->dg_items_max > 0 ? p->dg_items_max : 1; }
 
 template <typename R> static NufftK<R> base_args(Plan* p) {
     NufftK<R> k{};
@@ -504,13 +535,15 @@ static hs_status degrid_t(Plan* p, const DegridArgs& da, cudaStream_t s) {
     k.y = (const Cx<R>*)da.y;
     k.d = (Cx<R>*)da.d;
     k.part = da.part;
-    if (k.nblk_x == 0 || p->g.L == 0) return HS_OK;
-    dim3 grd(k.nblk_x, p->g.L);
+    if (p->n_dg_items == 0) return HS_OK;
+    const unsigned nb = (unsigned)p->n_dg_items;
+    const size_t sm = (size_t)DG_REG * DG_LDS * sizeof(Cx<R>);
+    const DgItem* items = (const DgItem*)p->dg_items;
     switch (da.mode) {
-        case DOUT_CALLER: k_degrid<R, NC, DOUT_CALLER><<<grd, 256, 0, s>>>(k); break;
-        case DOUT_SORTED: k_degrid<R, NC, DOUT_SORTED><<<grd, 256, 0, s>>>(k); break;
-        case DOUT_SORTED_U: k_degrid<R, NC, DOUT_SORTED_U><<<grd, 256, 0, s>>>(k); break;
-        case DOUT_PD: k_degrid<R, NC, DOUT_PD><<<grd, 256, 0, s>>>(k); break;
+        case DOUT_CALLER: k_degrid<R, NC, DOUT_CALLER><<<nb, 256, sm, s>>>(k, items); break;
+        case DOUT_SORTED: k_degrid<R, NC, DOUT_SORTED><<<nb, 256, sm, s>>>(k, items); break;
+        case DOUT_SORTED_U: k_degrid<R, NC, DOUT_SORTED_U><<<nb, 256, sm, s>>>(k, items); break;
+        case DOUT_PD: k_degrid<R, NC, DOUT_PD><<<nb, 256, sm, s>>>(k, items); break;
         default: return fail(HS_ERR_ARG, "degrid: bad mode");
     }
     HS_CHECK_LAUNCH();

@@ -144,6 +144,42 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
         for (int64_t r = 0; r < b - a; ++r) perm[a + r] = (int)(a + (int64_t)(keys[r] & 0xffffffffu));
     }
     HS_TRY(upload(p, (void**)&p->perm, perm));
+    // de-gridding work items: runs of one window-start tile in each channel's
+    // sorted range (cells before the fixed-point carry, as in the sort key), split
+    // into chunks of at most DEGRID_CHUNK visibilities; slot = l * items_max + k
+    {
+        std::vector<int> items;
+        std::vector<int> per_l(L, 0);
+        const int64_t ntl = (int64_t)g.ntx * g.nty;
+        for (int l = 0; l < L; ++l) {
+            const int64_t a = p->off_h[l], b = p->off_h[l + 1];
+            int64_t r = a;
+            while (r < b) {
+                auto tile_of = [&](int64_t rr) {
+                    const int64_t i = perm[rr];
+                    const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+                    return (int64_t)(k0y / TY) * g.ntx + k0x / TX;
+                };
+                const int64_t t = tile_of(r);
+                int64_t e = r + 1;
+                while (e < b && tile_of(e) == t) ++e;
+                for (int64_t c0 = r; c0 < e; c0 += DEGRID_CHUNK) {
+                    const int64_t c1 = std::min<int64_t>(e, c0 + DEGRID_CHUNK);
+                    items.insert(items.end(), {(int)(l * ntl + t), (int)c0, (int)c1, per_l[l]++});
+                }
+                r = e;
+            }
+        }
+        int mx = 1;
+        for (int l = 0; l < L; ++l) mx = std::max(mx, per_l[l]);
+        for (size_t k = 0; k < items.size(); k += 4) {
+            const int l = (int)(items[k] / ntl);
+            items[k + 3] += l * mx;
+        }
+        p->dg_items_max = mx;
+        p->n_dg_items = (int64_t)items.size() / 4;
+        HS_TRY(upload(p, &p->dg_items, items));
+    }
 
     if (p->prec == HS_F32) {
         std::vector<uint32_t> c((size_t)2 * M);
