@@ -307,6 +307,26 @@ HS_API hs_status hs_pd_graph_kernels(hs_pd_state_t state, int* out);
 HS_API hs_status hs_pd_nuclear_info(hs_pd_state_t state, double* sv_host, int* active_host,
                                     void* stream);
 
+/*
+ * hs_pd_reweight - weight update of the re-weighting outer loop (Sec. 3.5,
+ * Algorithm 1) from the state's current primal X:
+ *   w_l21[n] = gamma_l21 / (gamma_l21 + ||(Psi^dagger X)_n||_2)   (Eq. "weights-l21"),
+ *     n a row (basis, pixel) of the coefficient cube, norm across channels;
+ *     DEVICE 9 x ny x nx reals of the plan's precision, or NULL;
+ *   w_nuc[j] = gamma_nuc / (gamma_nuc + sigma_j(X))              (Eq. "weights-n"),
+ *     sigma_j the singular values of the N x L matrix X, descending;
+ *     DEVICE L doubles, or NULL (needs L <= 64);
+ *   sv_out: DEVICE L doubles receiving sigma_j, or NULL.
+ * Pass the buffers the state was created with as params->w_l21 / w_nuc to make
+ * the next iterations use the new weights (the state reads them in place).
+ * gamma_* must be finite and > 0 for the outputs requested. Asynchronous on
+ * `stream`; it uses the state's and plan's scratch, so it must not overlap an
+ * iteration of the same state. FP32 plans refine every eigenpair with a
+ * positive eigenvalue in FP64.
+ */
+HS_API hs_status hs_pd_reweight(hs_pd_state_t st, double gamma_l21, double gamma_nuc, void* w_l21,
+                         double* w_nuc, double* sv_out, void* stream);
+
 /* Number of iterations performed by a state. */
 HS_API hs_status hs_pd_iterations(hs_pd_state_t state, int64_t* out);
 

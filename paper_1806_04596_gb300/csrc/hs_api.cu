@@ -44,6 +44,7 @@ struct hs_pd_state {
     double* dpart = nullptr;   // de-gridding partial sums [L][nbx] (one slot per work item)
     float* warm = nullptr;     // L x L eigenvectors of the previous nuclear step (FP32 plans)
     double* sv = nullptr;      // L singular values of the last nuclear step
+    double* sv_rw = nullptr;   // L singular values of X for the re-weighting
     int* nact = nullptr;       // active count of the last nuclear step
     int nprim = 0;
     int nbx = 0;
@@ -445,6 +446,7 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     ALLOC(st->dpart, (size_t)L * st->nbx * sizeof(double));
     ALLOC(st->warm, (size_t)MAX_L_NUC * MAX_L_NUC * sizeof(float));
     ALLOC(st->sv, (size_t)std::max(L, 1) * sizeof(double));
+    ALLOC(st->sv_rw, (size_t)std::max(L, 1) * sizeof(double));
     ALLOC(st->nact, sizeof(int));
 #undef ALLOC
     auto cu = [&](cudaError_t ce, const char* what) -> hs_status {
@@ -652,6 +654,32 @@ hs_status hs_pd_nuclear_info(hs_pd_state_t st, double* sv_host, int* active_host
     if (active_host)
         HS_CHECK_CUDA(cudaMemcpyAsync(active_host, st->nact, sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    return HS_OK;
+}
+
+hs_status hs_pd_reweight(hs_pd_state_t st, double gamma_l21, double gamma_nuc, void* w_l21, double* w_nuc,
+                         double* sv_out, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_reweight: state is null");
+    if (w_l21 == nullptr && w_nuc == nullptr && sv_out == nullptr)
+        return fail(HS_ERR_ARG, "hs_pd_reweight: no output requested");
+    if (w_l21 && !(gamma_l21 > 0.0 && std::isfinite(gamma_l21)))
+        return fail(HS_ERR_ARG, "hs_pd_reweight: gamma_l21 must be finite and > 0");
+    if (w_nuc && !(gamma_nuc > 0.0 && std::isfinite(gamma_nuc)))
+        return fail(HS_ERR_ARG, "hs_pd_reweight: gamma_nuc must be finite and > 0");
+    Plan* p = st->p;
+    if ((w_nuc || sv_out) && p->g.L > MAX_L_NUC)
+        return fail(HS_ERR_ARG, "hs_pd_reweight: nuclear weights need L <= %d", MAX_L_NUC);
+    cudaStream_t s = S(stream);
+    if (w_l21) {   // Eq. "weights-l21" from Psi^dagger X (the state's analysis scratch)
+        HS_TRY(dwt_analysis(p, st->X, st->W, s));
+        HS_TRY(reweight_rows(p, st->W, gamma_l21, w_l21, s));
+    }
+    if (w_nuc || sv_out) {   // Eq. "weights-n" from the singular values of X
+        double* sv = sv_out ? sv_out : st->sv_rw;
+        HS_TRY(nuclear_svals(p, st->X, sv, s));
+        if (w_nuc) HS_TRY(reweight_sv(sv, p->g.L, gamma_nuc, w_nuc, s));
+    }
     return HS_OK;
 }
 

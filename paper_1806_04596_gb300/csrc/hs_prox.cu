@@ -465,6 +465,66 @@ hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* 
     return lowrank_apply_t<double>(p, X, Xadd, out, s);
 }
 
+// Singular values of the N x L matrix X (descending, FP64 buffer of L): the
+// Gram route of the nuclear prox with threshold 0 (every pair with a positive
+// eigenvalue is refined in FP64 in FP32 plans), cold-started.
+hs_status nuclear_svals(Plan* p, const void* X, double* sv_out, cudaStream_t s) {
+    const int L = p->g.L;
+    if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "singular values: L = %d exceeds %d", L, MAX_L_NUC);
+    const int64_t N = p->N();
+    const int P = L * (L + 1) / 2;
+    if (p->prec == HS_F32)
+        k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, nullptr, L, N, p->part);
+    else
+        k_gram<double><<<GRAM_CTAS, 256, 0, s>>>((const double*)X, nullptr, L, N, p->part);
+    HS_CHECK_LAUNCH();
+    k_gram_reduce<<<P, 128, 0, s>>>(p->part, GRAM_CTAS, L, p->gram);
+    HS_CHECK_LAUNCH();
+    if (p->prec == HS_F32) return eig_mixed_launch(p->gram, L, nullptr, 0.0, 1, p->eigf, sv_out, nullptr, nullptr, s);
+    return eig_f64_launch(p->gram, L, nullptr, 0.0, 1, p->eigf, sv_out, nullptr, s);
+}
+
+// ---------------------------------------------------------------- re-weighting (Algorithm 1)
+// w_n = gamma / (gamma + ||A_n||_2) for every row n = (basis, pixel) of the
+// coefficient cube A (norm across the L channels).
+template <typename R>
+__global__ void __launch_bounds__(256) k_rw_rows(const R* __restrict__ A, int L, int64_t N, double gamma,
+                                                R* __restrict__ w) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NB * N) return;
+    const int b = (int)(t / N);
+    const int64_t base = (int64_t)b * L * N + (t - (int64_t)b * N);
+    R s = 0;
+    for (int l = 0; l < L; ++l) {
+        const R q = A[base + (int64_t)l * N];
+        s = fma(q, q, s);
+    }
+    w[t] = (R)(gamma / (gamma + (double)sqrt(s)));
+}
+
+// w_j = gamma / (gamma + sigma_j)
+__global__ void k_rw_sv(const double* __restrict__ sv, int L, double gamma, double* __restrict__ w) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < L) w[j] = gamma / (gamma + sv[j]);
+}
+
+hs_status reweight_rows(Plan* p, const void* A, double gamma, void* w_out, cudaStream_t s) {
+    const int64_t N = p->N();
+    const unsigned g = nblk((int64_t)NB * N, 256);
+    if (p->prec == HS_F32)
+        k_rw_rows<float><<<g, 256, 0, s>>>((const float*)A, p->g.L, N, gamma, (float*)w_out);
+    else
+        k_rw_rows<double><<<g, 256, 0, s>>>((const double*)A, p->g.L, N, gamma, (double*)w_out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status reweight_sv(const double* sv, int L, double gamma, double* w_out, cudaStream_t s) {
+    k_rw_sv<<<(L + 127) / 128, 128, 0, s>>>(sv, L, gamma, w_out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
 hs_status prox_init() { return HS_OK; }
 
 int64_t gram_part_doubles(int L) { return (int64_t)(L * (L + 1) / 2) * GRAM_CTAS; }

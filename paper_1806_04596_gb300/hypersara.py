@@ -74,6 +74,7 @@ _SIGS = {
     "hs_pd_solve": ([_P, C.c_int, C.c_int, _P], C.c_int),
     "hs_pd_get": ([_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "hs_pd_iterations": ([_P, C.POINTER(C.c_int64)], C.c_int),
+    "hs_pd_reweight": ([_P, C.c_double, C.c_double, _P, _P, _P, _P], C.c_int),
     "hs_pd_graph_kernels": ([_P, C.POINTER(C.c_int)], C.c_int),
     "hs_pd_nuclear_info": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int), _P], C.c_int),
     "hs_time_stage": ([_P, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_float), _P], C.c_int),
@@ -311,6 +312,12 @@ class PDState:
         _check("hs_pd_nuclear_info", load().hs_pd_nuclear_info(self.h, sv, C.byref(n), _stream()))
         return np.array(sv[:]), n.value
 
+    def reweight(self, gamma_l21: float, gamma_nuc: float, w_l21=None, w_nuc=None, sv=None):
+        """hs_pd_reweight: Algorithm 1 weights from the current X into w_l21 (9 x ny x nx,
+        plan dtype) and w_nuc (L, FP64), and the singular values of X into sv."""
+        _check("hs_pd_reweight", load().hs_pd_reweight(self.h, float(gamma_l21), float(gamma_nuc), _ptr(w_l21),
+                                                       _ptr(w_nuc), _ptr(sv), _stream()))
+
     @property
     def graph_kernels(self) -> int:
         n = C.c_int()
@@ -333,6 +340,23 @@ class PDState:
             self.close()
         except Exception:
             pass
+
+
+def reweighted_solve(state: PDState, outer: int, inner: int, decay: float = 0.8, graph: bool = True):
+    """Algorithm 1: `outer` re-weights of `inner` PD iterations. The state must
+    have been created with weight buffers (w_l21, w_nuc tensors holding ones);
+    they are updated in place after every inner loop, gamma and gamma_bar
+    starting at 1 and multiplied by `decay` after each update."""
+    w_nuc, w_l21 = state._refs
+    if w_nuc is None or w_l21 is None:
+        raise ValueError("reweighted_solve needs a state created with w_nuc and w_l21 buffers")
+    gamma = gamma_bar = 1.0
+    for _ in range(outer):
+        state.solve(inner, graph)
+        state.reweight(gamma_bar, gamma, w_l21, w_nuc)
+        gamma *= decay
+        gamma_bar *= decay
+    return state
 
 
 # Functional names matching the C ABI ----------------------------------------
