@@ -15,6 +15,11 @@ kappa_2 = 1 / ||Psi^dagger||^2 and kappa_3 = 1 / ||U^{1/2} Phi||^2 the updates a
   step 22  X~    = 2 X - X_prev
   step 23  beta  = ||X - X_prev|| / ||X||
 
+Variants of Sec. 4.2 through the flags: LR (use_l21 = False), JAS
+(use_nuclear = False), and SARA (use_nuclear = False, sparsity = "l1": step 7
+with the per-coefficient l1 dual (I - S^{l1}) in place of the l2,1 one, which
+decouples the channels into L single-channel problems).
+
 Initial state: everything zero (the paper's "Given" does not fix it). Steps
 13-19 (adaptive bounds) are not applied: the simulations keep epsilon fixed.
 Data blocks: B = 1 per channel (M_l^b = I).
@@ -42,6 +47,7 @@ class PDParams:
     w_l21: object = 1.0            # scalar or (9, ny, nx) l2,1 row weights
     use_nuclear: bool = True
     use_l21: bool = True
+    sparsity: str = "l21"          # "l21" (joint, rows across channels) or "l1" (per channel, SARA)
 
 
 @dataclass
@@ -75,7 +81,10 @@ def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=No
     # steps 7-8: joint average sparsity dual and its synthesis
     if prm.use_l21:
         Q = st.A + wavelets.psi_adjoint_cube(Xt, prm.levels)
-        A = prox.l21_dual(Q, prm.w_l21, prm.mu * prm.psi_norm2)
+        if prm.sparsity == "l1":
+            A = prox.l1_dual(Q, prm.w_l21, prm.mu * prm.psi_norm2)
+        else:
+            A = prox.l21_dual(Q, prm.w_l21, prm.mu * prm.psi_norm2)
         At = wavelets.psi_cube(A, prm.levels)
     else:
         A = np.zeros_like(st.A)

@@ -78,6 +78,21 @@ def l21_dual(Q: np.ndarray, w_rows, thr: float) -> np.ndarray:
     return Q * f[:, None]
 
 
+def prox_l1(A: np.ndarray, w, thr: float) -> np.ndarray:
+    """Weighted l1 prox (soft thresholding) of every coefficient: sign(a) max(|a| - thr w, 0).
+    The SARA prior of the single-channel benchmark (Sec. 4.2): the sparsity
+    term of each channel on its own, no coupling across channels."""
+    lam = thr * np.broadcast_to(np.asarray(w, dtype=np.float64), A.shape)
+    return np.sign(A) * np.maximum(np.abs(A) - lam, 0.0)
+
+
+def l1_dual(Q: np.ndarray, w, thr: float) -> np.ndarray:
+    """(I - S^{l1}_{thr w})(Q): every coefficient clipped to [-thr w, thr w]
+    (the step-7 dual update with the l1 prior in place of l2,1)."""
+    lam = thr * np.broadcast_to(np.asarray(w, dtype=np.float64), Q.shape)
+    return np.clip(Q, -lam, lam)
+
+
 def proj_l2ball(z: np.ndarray, y: np.ndarray, eps: float) -> np.ndarray:
     """Projection onto B(y, eps) = {z : ||z - y||_2 <= eps} (Sec. 3.2, functions g_l)."""
     d = z - y

@@ -30,6 +30,13 @@ def weights_l21(X: np.ndarray, levels: int, gamma_bar: float) -> np.ndarray:
     return gamma_bar / (gamma_bar + prox.row_norms(A))
 
 
+def weights_l1(X: np.ndarray, levels: int, gamma_bar: float) -> np.ndarray:
+    """(9, L, ny, nx) per-coefficient weights of the SARA prior (the l1 analogue
+    of Eq. "weights-l21": each coefficient on its own)."""
+    A = wavelets.psi_adjoint_cube(X, levels)
+    return gamma_bar / (gamma_bar + np.abs(A))
+
+
 def weights_nuclear(X: np.ndarray, gamma: float) -> np.ndarray:
     """(L,) weights from the singular values of the N x L matrix of X."""
     L = X.shape[0]
@@ -47,7 +54,10 @@ def reweighted_solve(op, y, eps, prm: pd.PDParams, outer: int, inner: int, decay
     w21 = wn = None
     for _ in range(outer):
         st = pd.pd_solve(op, y, eps, p, inner, U=U, state=st)
-        w21 = weights_l21(st.X, prm.levels, gamma_bar)
+        if prm.sparsity == "l1":
+            w21 = weights_l1(st.X, prm.levels, gamma_bar)
+        else:
+            w21 = weights_l21(st.X, prm.levels, gamma_bar)
         wn = weights_nuclear(st.X, gamma)
         p = dataclasses.replace(prm, w_l21=w21, w_nuc=wn)
         gamma *= decay

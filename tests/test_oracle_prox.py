@@ -136,3 +136,21 @@ def test_l2ball_dual_with_preconditioner():
     d = z - y
     ref = np.sqrt(U) * d * max(0.0, 1 - eps / np.linalg.norm(d))
     np.testing.assert_allclose(v, ref, atol=1e-13)
+
+
+def test_l1_prox_and_dual_closed_forms_and_moreau():
+    """Soft thresholding (SARA prior): known values, and prox + dual = identity."""
+    q = np.array([[-3.0, -0.5, 0.0, 0.2, 2.5]])
+    w = np.array([[1.0, 1.0, 2.0, 0.1, 0.5]])
+    np.testing.assert_array_equal(prox.prox_l1(q, w, 1.0), [[-2.0, 0.0, 0.0, 0.1, 2.0]])
+    np.testing.assert_array_equal(prox.l1_dual(q, w, 1.0), [[-1.0, -0.5, 0.0, 0.1, 0.5]])
+    rng = np.random.default_rng(8)
+    Q = rng.standard_normal((9, 3, 8, 8))
+    W = rng.uniform(0.1, 2.0, Q.shape)
+    np.testing.assert_allclose(prox.prox_l1(Q, W, 0.7) + prox.l1_dual(Q, W, 0.7), Q, rtol=0, atol=1e-15)
+    # the l1 prox is the minimiser of 0.5 ||a - q||^2 + thr sum w |a|: check optimality per entry
+    A = prox.prox_l1(Q, W, 0.7)
+    g = A - Q
+    nz = A != 0
+    np.testing.assert_allclose(g[nz], -0.7 * W[nz] * np.sign(A[nz]), rtol=0, atol=1e-14)
+    assert np.all(np.abs(g[~nz]) <= 0.7 * W[~nz] + 1e-15)

@@ -78,3 +78,14 @@ def test_outer_loop_structure():
     np.testing.assert_allclose(st2.X, ref2.X, rtol=0, atol=1e-15)
     s = np.linalg.svd(ref2.X.reshape(3, -1).T, compute_uv=False)
     np.testing.assert_allclose(wnb, 0.5 / (0.5 + s), rtol=1e-12)
+
+
+def test_l1_weights_single_pixel():
+    """SARA weights are per coefficient: the bright pixel's Dirac coefficient of
+    channel l is a_l / 3."""
+    a = np.array([0.3, 1.2])
+    X = np.zeros((2, 16, 16))
+    X[:, 4, 4] = a
+    w = reweight.weights_l1(X, 1, 0.5)
+    np.testing.assert_allclose(w[0, :, 4, 4], 0.5 / (0.5 + a / 3), rtol=1e-13)
+    assert w.shape == (9, 2, 16, 16) and np.all(w[0, :, 0, 0] == 1.0)
