@@ -252,7 +252,10 @@ typedef struct {
     int use_nuclear;    /* 0 drops the low-rankness prior (LR / JAS variants) */
     int use_l21;        /* 0 drops the joint-sparsity prior */
     const double* w_nuc;   /* DEVICE L doubles (nuclear weights) or NULL = 1; referenced, not copied */
-    const void* w_l21;     /* DEVICE 9 x ny x nx reals (row weights) or NULL = 1; referenced */
+    const void* w_l21;     /* DEVICE 9 x ny x nx reals (row weights) or NULL = 1; referenced
+                              (sparsity = 1: 9 x L x ny x nx per-coefficient weights) */
+    int sparsity;          /* 0: l2,1 rows across channels (HyperSARA, JAS); 1: l1 per
+                              coefficient (SARA, Sec. 4.2: the channels decouple) */
 } hs_pd_params;
 
 /*

@@ -407,6 +407,8 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
         !std::isfinite(prm->kappa3) || !(prm->mu >= 0.0) || !(prm->psi_norm2 > 0.0))
         return fail(HS_ERR_ARG, "hs_pd_state_create: invalid parameters");
     Plan* p = plan->p;
+    if (prm->sparsity != 0 && prm->sparsity != 1)
+        return fail(HS_ERR_ARG, "hs_pd_state_create: sparsity must be 0 (l2,1) or 1 (l1)");
     if (prm->use_nuclear && p->g.L > MAX_L_NUC)
         return fail(HS_ERR_ARG, "hs_pd_state_create: nuclear prior needs L <= %d", MAX_L_NUC);
     cudaStream_t s = S(stream);
@@ -535,7 +537,10 @@ static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
     if (q.use_l21) {     // steps 7-8
         HS_TRY(dwt_analysis(p, st->Xt, st->W, st->side2));
         // A_d = (I - S^{l21}_{w mu ||Psi||^2})(A_d + Psi_d^dagger X~)
-        HS_TRY(l21_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side2));
+        if (q.sparsity == 1)   // SARA: per-coefficient l1 dual
+            HS_TRY(l1_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side2));
+        else
+            HS_TRY(l21_apply(p, st->A, st->W, q.w_l21, q.mu * q.psi_norm2, 1, st->A, st->side2));
         HS_TRY(dwt_synthesis(p, st->A, st->At, st->side2));
     }
     HS_CHECK_CUDA(cudaEventRecord(st->ev_join2, st->side2));
@@ -673,7 +678,8 @@ hs_status hs_pd_reweight(hs_pd_state_t st, double gamma_l21, double gamma_nuc, v
     cudaStream_t s = S(stream);
     if (w_l21) {   // Eq. "weights-l21" from Psi^dagger X (the state's analysis scratch)
         HS_TRY(dwt_analysis(p, st->X, st->W, s));
-        HS_TRY(reweight_rows(p, st->W, gamma_l21, w_l21, s));
+        if (st->prm.sparsity == 1) HS_TRY(reweight_coef(p, st->W, gamma_l21, w_l21, s));
+        else HS_TRY(reweight_rows(p, st->W, gamma_l21, w_l21, s));
     }
     if (w_nuc || sv_out) {   // Eq. "weights-n" from the singular values of X
         double* sv = sv_out ? sv_out : st->sv_rw;

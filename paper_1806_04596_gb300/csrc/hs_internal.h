@@ -184,6 +184,9 @@ hs_status l21_norm(Plan* p, const void* A, const void* w_rows, double* out_dev, 
 hs_status nuclear_svals(Plan* p, const void* X, double* sv_out, cudaStream_t s);
 hs_status reweight_rows(Plan* p, const void* A, double gamma, void* w_out, cudaStream_t s);
 hs_status reweight_sv(const double* sv, int L, double gamma, double* w_out, cudaStream_t s);
+hs_status reweight_coef(Plan* p, const void* A, double gamma, void* w_out, cudaStream_t s);
+hs_status l1_apply(Plan* p, const void* A, const void* Wadd, const void* w, double thr, int dual, void* out,
+                   cudaStream_t s);
 hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
                         int dual, void* out, double* sv_out, float* warm, int* r_out, cudaStream_t s);
 // FP32 plans: mixed-precision eigendecomposition of the Gram matrix (hs_eig.cu).

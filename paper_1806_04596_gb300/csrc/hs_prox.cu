@@ -12,6 +12,8 @@
 //            X~ = 2 X - X_prev, beta partial sums.
 #include <cmath>
 
+#include <algorithm>
+
 #include "hs_device.cuh"
 #include "hs_internal.h"
 
@@ -121,6 +123,35 @@ hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows
         else HS_L21(double, 0);
     }
 #undef HS_L21
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+// SARA prior (Sec. 4.2): every coefficient on its own. Dual form (step 7 with
+// the l1 norm): out = clip(A + W, -thr w, thr w); prox form: soft threshold.
+template <typename R>
+__global__ void __launch_bounds__(256) k_l1(const R* __restrict__ A, const R* __restrict__ W,
+                                           const R* __restrict__ w, R thr, int dual, R* __restrict__ out,
+                                           int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        R q = A[i];
+        if (W) q += W[i];
+        const R lam = thr * (w ? w[i] : (R)1);
+        const R c = fmin(fmax(q, -lam), lam);
+        out[i] = dual ? c : q - c;
+    }
+}
+
+hs_status l1_apply(Plan* p, const void* A, const void* Wadd, const void* w, double thr, int dual, void* out,
+                   cudaStream_t s) {
+    const int64_t n = (int64_t)NB * p->g.L * p->N();
+    const unsigned g = std::min<unsigned>(nblk(n, 256), 152u * 16u);
+    if (p->prec == HS_F32)
+        k_l1<float><<<g, 256, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w, (float)thr, dual,
+                                      (float*)out, n);
+    else
+        k_l1<double><<<g, 256, 0, s>>>((const double*)A, (const double*)Wadd, (const double*)w, thr, dual,
+                                       (double*)out, n);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
@@ -500,6 +531,25 @@ __global__ void __launch_bounds__(256) k_rw_rows(const R* __restrict__ A, int L,
         s = fma(q, q, s);
     }
     w[t] = (R)(gamma / (gamma + (double)sqrt(s)));
+}
+
+// SARA weights: w_i = gamma / (gamma + |a_i|) for every coefficient.
+template <typename R>
+__global__ void __launch_bounds__(256) k_rw_coef(const R* __restrict__ A, int64_t n, double gamma,
+                                                R* __restrict__ w) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = (R)(gamma / (gamma + fabs((double)A[i])));
+}
+
+hs_status reweight_coef(Plan* p, const void* A, double gamma, void* w_out, cudaStream_t s) {
+    const int64_t n = (int64_t)NB * p->g.L * p->N();
+    const unsigned g = std::min<unsigned>(nblk(n, 256), 152u * 16u);
+    if (p->prec == HS_F32)
+        k_rw_coef<float><<<g, 256, 0, s>>>((const float*)A, n, gamma, (float*)w_out);
+    else
+        k_rw_coef<double><<<g, 256, 0, s>>>((const double*)A, n, gamma, (double*)w_out);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
 }
 
 // w_j = gamma / (gamma + sigma_j)

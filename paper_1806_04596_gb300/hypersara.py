@@ -46,7 +46,7 @@ class PDParams(C.Structure):
     _fields_ = [("tau", C.c_double), ("kappa1", C.c_double), ("kappa2", C.c_double),
                 ("kappa3", C.c_double), ("mu", C.c_double), ("psi_norm2", C.c_double),
                 ("use_nuclear", C.c_int), ("use_l21", C.c_int),
-                ("w_nuc", C.c_void_p), ("w_l21", C.c_void_p)]
+                ("w_nuc", C.c_void_p), ("w_l21", C.c_void_p), ("sparsity", C.c_int)]
 
 
 _P = C.c_void_p
@@ -277,12 +277,18 @@ class PDState:
 
     def __init__(self, plan: Plan, Y, eps, *, tau: float = 0.33, kappa1: float = 1.0,
                  kappa2: float = 1.0, kappa3: float = 1.0, mu: float = 0.0, psi_norm2: float = 1.0,
-                 use_nuclear: bool = True, use_l21: bool = True, w_nuc=None, w_l21=None):
+                 use_nuclear: bool = True, use_l21: bool = True, w_nuc=None, w_l21=None,
+                 sparsity: str = "l21"):
+        """sparsity: "l21" (rows across channels: HyperSARA, JAS) or "l1" (per
+        coefficient: SARA; w_l21 is then 9 x L x ny x nx)."""
+        if sparsity not in ("l21", "l1"):
+            raise ValueError("sparsity must be 'l21' or 'l1'")
         self.plan = plan
+        self.sparsity = sparsity
         self._refs = (w_nuc, w_l21)   # the state references these buffers
         prm = PDParams(tau, kappa1, kappa2, kappa3, mu, psi_norm2, int(use_nuclear), int(use_l21),
                        None if w_nuc is None else w_nuc.data_ptr(),
-                       None if w_l21 is None else w_l21.data_ptr())
+                       None if w_l21 is None else w_l21.data_ptr(), 1 if sparsity == "l1" else 0)
         h = C.c_void_p()
         _check("hs_pd_state_create", load().hs_pd_state_create(plan.h, _ptr(Y), _ptr(eps), C.byref(prm),
                                                                C.byref(h), _stream()))
@@ -346,10 +352,12 @@ def reweighted_solve(state: PDState, outer: int, inner: int, decay: float = 0.8,
     """Algorithm 1: `outer` re-weights of `inner` PD iterations. The state must
     have been created with weight buffers (w_l21, w_nuc tensors holding ones);
     they are updated in place after every inner loop, gamma and gamma_bar
-    starting at 1 and multiplied by `decay` after each update."""
+    starting at 1 and multiplied by `decay` after each update. Without a w_nuc
+    buffer only the sparsity weights are updated (JAS, SARA)."""
     w_nuc, w_l21 = state._refs
-    if w_nuc is None or w_l21 is None:
-        raise ValueError("reweighted_solve needs a state created with w_nuc and w_l21 buffers")
+    if w_l21 is None:
+        raise ValueError("reweighted_solve needs a state created with a w_l21 buffer (and w_nuc when the "
+                         "nuclear prior is used)")
     gamma = gamma_bar = 1.0
     for _ in range(outer):
         state.solve(inner, graph)

@@ -85,3 +85,38 @@ def test_reweighted_solve_tracks_oracle_fp64():
     assert rel(host(st.get()[0]), ref.X) <= 1e-11
     assert rel(host(w_l21), r21) <= 1e-11
     np.testing.assert_allclose(host(w_nuc), rnuc, rtol=1e-9)
+
+
+def _sara_state(inp, prob, prm, prec, weights=False):
+    import torch
+    from paper_1806_04596_gb300 import hypersara as hs
+    plan = hs.Plan(inp.nx, inp.ny, inp.offsets, dev(inp.uv, prec), levels=prm.levels, prec=prec)
+    rt = torch.float32 if prec == "f32" else torch.float64
+    w = torch.ones((9, inp.L, inp.ny, inp.nx), dtype=rt, device="cuda") if weights else None
+    st = hs.PDState(plan, dev(prob.y, prec, True), torch.tensor(prob.eps, dtype=torch.float64, device="cuda"),
+                    tau=prm.tau, kappa3=prm.kappa3, mu=prm.mu, use_nuclear=False, w_l21=w, sparsity="l1")
+    return plan, st, w
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 1e-4)])
+def test_sara_variant_tracks_oracle(prec, tol):
+    """SARA (Sec. 4.2): per-channel l1 prior, no nuclear term."""
+    import dataclasses
+    inp, prob, prm = _problem(prec)
+    prm = dataclasses.replace(prm, use_nuclear=False, sparsity="l1")
+    plan, st, _ = _sara_state(inp, prob, prm, prec)
+    st.solve(20, graph=True)
+    ref = pd.pd_solve(prob.op, prob.y, prob.eps, prm, 20)
+    assert rel(host(st.get()[0]), ref.X) <= tol
+
+
+def test_sara_reweighted_fp64():
+    import dataclasses
+    from paper_1806_04596_gb300 import hypersara as hs
+    inp, prob, prm = _problem("f64")
+    prm = dataclasses.replace(prm, use_nuclear=False, sparsity="l1")
+    plan, st, w = _sara_state(inp, prob, prm, "f64", weights=True)
+    hs.reweighted_solve(st, outer=2, inner=10, decay=0.7)
+    ref, r1, _ = reweight.reweighted_solve(prob.op, prob.y, prob.eps, prm, outer=2, inner=10, decay=0.7)
+    assert rel(host(st.get()[0]), ref.X) <= 1e-11
+    assert rel(host(w), r1) <= 1e-11
