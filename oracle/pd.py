@@ -20,6 +20,20 @@ Variants of Sec. 4.2 through the flags: LR (use_l21 = False), JAS
 with the per-coefficient l1 dual (I - S^{l1}) in place of the l2,1 one, which
 decouples the channels into L single-channel problems).
 
+Data blocks (Sec. 2.1, M_l^b): `blocks` are offsets into the visibility
+vector (caller order) containing every channel boundary; each block has its
+own bound epsilon_l^b and ball projection (steps 10-11). Without blocks, one
+block per channel.
+
+Adaptive bounds (steps 13-19, Sec. 3.6), enabled by `adapt`: with
+rho_b = ||y_b - Phibar_b X~^{(t-1)}|| (the data residual of the block at the
+extrapolated image this iteration uses), if beta^{(t-1)} < lambda_1 and
+t - vartheta_b > vartheta_bar and |rho_b - eps_b| / eps_b > lambda_2 then
+eps_b <- lambda_3 rho_b + (1 - lambda_3) eps_b and vartheta_b <- t. Readings:
+t counts iterations from 1, vartheta starts at 0, beta^{(0)} is undefined (the
+first iteration never adjusts), and the new bounds serve from the next
+iteration (step 11 uses eps^{(t-1)}).
+
 Initial state: everything zero (the paper's "Given" does not fix it). Steps
 13-19 (adaptive bounds) are not applied: the simulations keep epsilon fixed.
 Data blocks: B = 1 per channel (M_l^b = I).
@@ -51,6 +65,15 @@ class PDParams:
 
 
 @dataclass
+class AdaptParams:
+    """Steps 13-19 (values of Sec. 3.6 / Appendix A used in the paper's runs)."""
+    lambda1: float = 5e-4
+    lambda2: float = 0.01
+    lambda3: float = 0.618
+    min_gap: int = 100             # vartheta_bar
+
+
+@dataclass
 class PDState:
     X: np.ndarray
     Xt: np.ndarray
@@ -60,6 +83,9 @@ class PDState:
     t: int = 0
     beta: float = float("nan")
     rho: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    eps: np.ndarray | None = None      # current bounds per block (adaptive runs)
+    theta: np.ndarray | None = None    # iteration of each block's last bound update
+    resid: np.ndarray = field(default_factory=lambda: np.zeros(0))
 
 
 def init_state(L: int, ny: int, nx: int, M_total: int) -> PDState:
@@ -69,8 +95,11 @@ def init_state(L: int, ny: int, nx: int, M_total: int) -> PDState:
                    v=np.zeros(M_total, dtype=np.complex128))
 
 
-def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=None) -> PDState:
-    """One iteration of Algorithm 2 (returns a new state)."""
+def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=None, blocks=None,
+            adapt: AdaptParams | None = None) -> PDState:
+    """One iteration of Algorithm 2 (returns a new state). eps: one bound per
+    block (per channel without blocks); with `adapt` the state carries the
+    current bounds."""
     L = st.X.shape[0]
     Xt = st.Xt
     # step 5: low rankness dual
@@ -89,17 +118,33 @@ def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=No
     else:
         A = np.zeros_like(st.A)
         At = np.zeros_like(st.X)
-    # steps 4, 10-12: data fidelity duals
+    # steps 4, 10-12: data fidelity duals, one ball per block
     PhiXt = op.forward(Xt)
+    bo = np.asarray(op.offsets if blocks is None else blocks)
+    nb = len(bo) - 1
+    eps_cur = np.asarray(eps, dtype=np.float64) if st.eps is None else st.eps
     v = np.empty_like(st.v)
-    rho = np.empty(L)
-    for l in range(L):
-        a, b = op.offsets[l], op.offsets[l + 1]
+    rho = np.empty(nb)
+    resid = np.empty(nb)
+    for k in range(nb):
+        a, b = bo[k], bo[k + 1]
         Ul = None if U is None else U[a:b]
         vbar = st.v[a:b] + (PhiXt[a:b] if Ul is None else Ul * PhiXt[a:b])
         z = vbar if Ul is None else vbar / np.sqrt(Ul)
-        rho[l] = np.sqrt(np.sum(np.abs(z - y[a:b]) ** 2))
-        v[a:b] = prox.l2ball_dual(vbar, y[a:b], eps[l], Ul)
+        rho[k] = np.sqrt(np.sum(np.abs(z - y[a:b]) ** 2))
+        resid[k] = np.sqrt(np.sum(np.abs(y[a:b] - PhiXt[a:b]) ** 2))
+        v[a:b] = prox.l2ball_dual(vbar, y[a:b], eps_cur[k], Ul)
+    # steps 13-19: adjust the bounds (used from the next iteration)
+    t = st.t + 1
+    eps_new, theta = eps_cur, st.theta
+    if adapt is not None:
+        theta = np.zeros(nb, dtype=np.int64) if st.theta is None else st.theta.copy()
+        eps_new = eps_cur.copy()
+        for k in range(nb):
+            if (st.beta < adapt.lambda1 and t - theta[k] > adapt.min_gap
+                    and abs(resid[k] - eps_cur[k]) / eps_cur[k] > adapt.lambda2):
+                eps_new[k] = adapt.lambda3 * resid[k] + (1.0 - adapt.lambda3) * eps_cur[k]
+                theta[k] = t
     # steps 20-23: primal update
     Gd = op.adjoint(v)
     G = prm.kappa1 * P + prm.kappa2 * At + prm.kappa3 * Gd
@@ -107,14 +152,15 @@ def pd_step(st: PDState, op, y: np.ndarray, eps: np.ndarray, prm: PDParams, U=No
     Xtn = 2.0 * Xn - st.X
     nx_ = np.sqrt(np.sum(Xn * Xn))
     beta = np.sqrt(np.sum((Xn - st.X) ** 2)) / nx_ if nx_ > 0 else float("inf")
-    return PDState(X=Xn, Xt=Xtn, P=P, A=A, v=v, t=st.t + 1, beta=beta, rho=rho)
+    return PDState(X=Xn, Xt=Xtn, P=P, A=A, v=v, t=t, beta=beta, rho=rho,
+                   eps=eps_new if adapt is not None else st.eps, theta=theta, resid=resid)
 
 
 def pd_solve(op, y, eps, prm: PDParams, iters: int, U=None, state: PDState | None = None,
-             callback=None) -> PDState:
+             callback=None, blocks=None, adapt: AdaptParams | None = None) -> PDState:
     st = state if state is not None else init_state(op.L, op.ny, op.nx, int(op.offsets[-1]))
     for _ in range(iters):
-        st = pd_step(st, op, y, eps, prm, U)
+        st = pd_step(st, op, y, eps, prm, U, blocks, adapt)
         if callback is not None:
             callback(st)
     return st
