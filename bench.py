@@ -348,6 +348,41 @@ def run_ours(a):
     h2d = M * y_dev.element_size()
     d2h = 8 + 8 * L
 
+    # model variants and the re-weighting step on the same problem (FP32, graph replay)
+    def _iter_rate(state, k):
+        state.solve(2, graph=True)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        state.solve(k, graph=True)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        return k / (g0.elapsed_time(g1) / 1e3)
+
+    kv = max(5, min(a.steps // 4, 200))
+    variants = {}
+    for name, kw in (("lr", dict(use_l21=False)), ("jas", dict(use_nuclear=False)),
+                     ("sara", dict(use_nuclear=False, sparsity="l1"))):
+        sv_ = hs.PDState(plan, P.y, P.eps, tau=0.33, kappa3=P.kappa3, mu=P.mu, **kw)
+        variants[name] = {"value": _iter_rate(sv_, kv), "unit": UNIT}
+        sv_.close()
+    w21 = torch.ones((9, plan.ny, plan.nx), dtype=torch.float32, device="cuda")
+    wnu = torch.ones(L, dtype=torch.float64, device="cuda")
+    st_rw = hs.PDState(plan, P.y, P.eps, tau=0.33, kappa3=P.kappa3, mu=P.mu, w_nuc=wnu, w_l21=w21)
+    st_rw.solve(20, graph=True)
+    torch.cuda.synchronize()
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(5):
+        st_rw.reweight(0.8, 0.8, w21, wnu)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    variants["reweight_ms"] = r0.elapsed_time(r1) / 5
+    variants["reweighted_lrjas_iter_per_s"] = _iter_rate(st_rw, kv)
+    st_rw.close()
+
     # plain FP64 GPU form of the same iteration
     fp64 = None
     if not a.no_fp64:
@@ -388,6 +423,7 @@ def run_ours(a):
         "clocks": clocks,
         "asnr_db": asnr, "beta": beta, "mu": P.mu, "kappa3": P.kappa3,
         "fp64": fp64,
+        "variants": variants,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
