@@ -9,8 +9,9 @@
  *   - SARA dictionary Psi^dagger / Psi: Dirac + Daubechies 1-8 (Sec. 2.3);
  *   - proximity operators (Sec. 3.3, Eqs. "proj-plus", "prox-L*", "prox-L21")
  *     and their Moreau duals (Eq. "md");
- *   - one iteration of the preconditioned primal-dual algorithm (Algorithm 2,
- *     steps 2-12 and 20-23, fixed l2 bounds, one data block per channel).
+ *   - one iteration of the preconditioned primal-dual algorithm (Algorithm 2:
+ *     steps 2-23, data blocks, fixed or adaptive l2 bounds), its variants
+ *     (Sec. 4.2) and the re-weighting outer loop (Algorithm 1).
  *
  * Conventions shared by every entry point
  *   Precision   a plan is FP32 (HS_F32: real = float, complex = float2 {re, im})
@@ -111,6 +112,20 @@ HS_API hs_status hs_plan_create(hs_plan_t* out, int nx, int ny, int L, const int
                          int oversample, int J, double kb_beta, int wavelet_levels,
                          hs_prec prec, unsigned flags, void* stream);
 
+/*
+ * hs_plan_create_blocks - hs_plan_create with intra-channel data blocks
+ * (Sec. 2.1, masks M_l^b): block_offsets, HOST nblocks + 1 int64, splits the
+ * visibility vector (caller order) into contiguous blocks; it runs from 0 to
+ * the total, is nondecreasing and contains every channel boundary of
+ * vis_offsets (so nblocks >= L). PD states on the plan then keep one l2 bound,
+ * one ball projection and one residual per block (eps and rho of nblocks
+ * values). hs_plan_create is this call with one block per channel.
+ */
+HS_API hs_status hs_plan_create_blocks(hs_plan_t* out, int nx, int ny, int L, const int64_t* vis_offsets,
+                                int nblocks, const int64_t* block_offsets, const void* uv, const void* weights,
+                                const void* precond, int oversample, int J, double kb_beta,
+                                int wavelet_levels, hs_prec prec, unsigned flags, void* stream);
+
 /* Frees everything the plan owns. The caller must make sure no work using the
  * plan is still running. NULL is accepted. */
 HS_API hs_status hs_plan_destroy(hs_plan_t plan);
@@ -125,6 +140,7 @@ typedef struct {
     double kb_beta;
     double kb_fit_max_err;        /* max |poly - phi| / phi(0) of the kernel fit */
     int64_t device_bytes;         /* device memory held by the plan */
+    int nblocks;                  /* data blocks (L unless created with hs_plan_create_blocks) */
 } hs_plan_info_t;
 
 HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);
@@ -261,7 +277,8 @@ typedef struct {
 /*
  * hs_pd_state_create - primal-dual state for Algorithm 2 with one block per
  * channel and fixed l2 bounds. Y: DEVICE total complex data y_l (caller order,
- * copied). eps: DEVICE L doubles (copied). All primal and dual variables start
+ * copied). eps: DEVICE nblocks doubles, one l2 bound per data block (nblocks =
+ * L unless the plan has blocks; copied). All primal and dual variables start
  * at zero. The state keeps references to params->w_nuc / w_l21, which must stay
  * valid while it is used. Errors: HS_ERR_ARG, HS_ERR_NOMEM, HS_ERR_CUDA.
  */
@@ -272,7 +289,7 @@ HS_API hs_status hs_pd_state_destroy(hs_pd_state_t state);
 
 /*
  * hs_pd_set_data - replace the data y_l (DEVICE total complex, caller order) and
- * the bounds eps (DEVICE L doubles) of a state, keeping its primal and dual
+ * the bounds eps (DEVICE nblocks doubles) of a state, keeping its primal and dual
  * variables (warm start on new data of the same coverage). Asynchronous.
  */
 HS_API hs_status hs_pd_set_data(hs_pd_state_t state, const void* Y, const double* eps, void* stream);
@@ -290,8 +307,8 @@ HS_API hs_status hs_pd_solve(hs_pd_state_t state, int iters, int graph, void* st
 /*
  * hs_pd_get - copy the current primal estimate X (DEVICE L x ny x nx, may be
  * NULL) and the last iteration's diagnostics: *beta_host = ||X - X_prev|| / ||X||
- * (Algorithm 2 step 23) and rho_host[l] = ||U^{-1/2} vbar_l - y_l|| (HOST L
- * doubles, may be NULL). Synchronises the stream when beta_host or rho_host is
+ * (Algorithm 2 step 23) and rho_host[b] = ||U^{-1/2} vbar_b - y_b|| per data
+ * block (HOST nblocks doubles, may be NULL). Synchronises the stream when beta_host or rho_host is
  * given.
  */
 HS_API hs_status hs_pd_get(hs_pd_state_t state, void* X, double* beta_host, double* rho_host,
@@ -332,6 +349,31 @@ HS_API hs_status hs_pd_reweight(hs_pd_state_t st, double gamma_l21, double gamma
 
 /* Number of iterations performed by a state. */
 HS_API hs_status hs_pd_iterations(hs_pd_state_t state, int64_t* out);
+
+/*
+ * Adaptive l2 bounds (Algorithm 2 steps 13-19, Sec. 3.6). Each iteration t
+ * (counted from 1) computes rho_b = ||y_b - Phibar_b X~|| per data block at the
+ * extrapolated image it uses; if beta of the previous iteration < lambda1,
+ * t - vartheta_b > min_gap and |rho_b - eps_b| / eps_b > lambda2, the bound
+ * becomes lambda3 rho_b + (1 - lambda3) eps_b (used from the next iteration)
+ * and vartheta_b = t. The first iteration never adjusts (beta undefined).
+ * hs_pd_set_adaptive(st, NULL) or enable = 0 switches it off; changing it
+ * re-captures the iteration graph at the next hs_pd_solve. The paper's values:
+ * lambda1 = 5e-4, lambda2 = 0.01, lambda3 = 0.618, min_gap = 100.
+ */
+typedef struct {
+    int enable;
+    double lambda1, lambda2, lambda3;
+    int64_t min_gap;   /* vartheta_bar */
+} hs_adapt_params;
+
+HS_API hs_status hs_pd_set_adaptive(hs_pd_state_t st, const hs_adapt_params* params);
+
+/* Current bounds eps_b, last residuals rho_b = ||y_b - Phibar_b X~|| (adaptive
+ * runs) and vartheta_b per data block, copied to HOST arrays of nblocks
+ * entries (each may be NULL); synchronises the stream. */
+HS_API hs_status hs_pd_bounds(hs_pd_state_t st, double* eps_host, double* resid_host, int64_t* theta_host,
+                       void* stream);
 
 /* Stages of the measurement path that hs_time_stage can launch alone. */
 typedef enum {

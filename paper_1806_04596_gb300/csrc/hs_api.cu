@@ -9,9 +9,10 @@
 
 namespace hs {
 const char* last_error();
-hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, const void* uv,
-                      const void* weights, const void* precond, int oversample, int J, double kb_beta,
-                      int levels, hs_prec prec, unsigned flags, cudaStream_t s);
+hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, int nblocks,
+                      const int64_t* block_offsets, const void* uv, const void* weights, const void* precond,
+                      int oversample, int J, double kb_beta, int levels, hs_prec prec, unsigned flags,
+                      cudaStream_t s);
 void plan_free(Plan* p);
 }  // namespace hs
 
@@ -45,6 +46,11 @@ struct hs_pd_state {
     float* warm = nullptr;     // L x L eigenvectors of the previous nuclear step (FP32 plans)
     double* sv = nullptr;      // L singular values of the last nuclear step
     double* sv_rw = nullptr;   // L singular values of X for the re-weighting
+    double* rpart = nullptr;   // de-gridding partial ||y - Phi x~||^2 [nblk][nbx] (adaptive bounds)
+    int64_t* theta = nullptr;  // nblk: iteration of each block's last bound update
+    int64_t* tcnt = nullptr;   // completed iterations (device)
+    double* resid = nullptr;   // nblk: ||y_b - Phi_b x~|| of the last iteration (adaptive bounds)
+    hs_adapt_params adapt{};   // adaptive bounds, off unless set
     int* nact = nullptr;       // active count of the last nuclear step
     int nprim = 0;
     int nbx = 0;
@@ -88,12 +94,22 @@ hs_status hs_plan_create(hs_plan_t* out, int nx, int ny, int L, const int64_t* v
                          const void* uv, const void* weights, const void* precond, int oversample,
                          int J, double kb_beta, int wavelet_levels, hs_prec prec, unsigned flags,
                          void* stream) {
+    return hs_plan_create_blocks(out, nx, ny, L, vis_offsets, 0, nullptr, uv, weights, precond, oversample, J,
+                                 kb_beta, wavelet_levels, prec, flags, stream);
+}
+
+hs_status hs_plan_create_blocks(hs_plan_t* out, int nx, int ny, int L, const int64_t* vis_offsets, int nblocks,
+                                const int64_t* block_offsets, const void* uv, const void* weights,
+                                const void* precond, int oversample, int J, double kb_beta, int wavelet_levels,
+                                hs_prec prec, unsigned flags, void* stream) {
     clear_error();
     if (out == nullptr) return fail(HS_ERR_ARG, "hs_plan_create: out is null");
     *out = nullptr;
+    if ((block_offsets == nullptr) != (nblocks == 0))
+        return fail(HS_ERR_ARG, "hs_plan_create_blocks: block_offsets and nblocks must be given together");
     Plan* p = nullptr;
-    HS_TRY(plan_create(&p, nx, ny, L, vis_offsets, uv, weights, precond, oversample, J, kb_beta,
-                       wavelet_levels, prec, flags, S(stream)));
+    HS_TRY(plan_create(&p, nx, ny, L, vis_offsets, nblocks, block_offsets, uv, weights, precond, oversample, J,
+                       kb_beta, wavelet_levels, prec, flags, S(stream)));
     hs_plan* h = new (std::nothrow) hs_plan;
     if (h == nullptr) {
         plan_free(p);
@@ -138,6 +154,7 @@ hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info) {
     info->kb_beta = p->beta;
     info->kb_fit_max_err = p->kb_fit_err;
     info->device_bytes = p->device_bytes;
+    info->nblocks = p->nblk;
     return HS_OK;
 }
 
@@ -438,14 +455,19 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     ALLOC(st->v, M * cs);
     ALLOC(st->y, M * cs);
     ALLOC(st->d, M * cs);
-    ALLOC(st->eps, L * sizeof(double));
-    ALLOC(st->rho, L * sizeof(double));
-    ALLOC(st->scale, L * rs);
+    const int nb = p->nblk;   // data blocks (one per channel unless the plan has blocks)
+    ALLOC(st->eps, nb * sizeof(double));
+    ALLOC(st->rho, nb * sizeof(double));
+    ALLOC(st->scale, nb * rs);
+    ALLOC(st->theta, nb * sizeof(int64_t));
+    ALLOC(st->resid, nb * sizeof(double));
+    ALLOC(st->tcnt, sizeof(int64_t));
     ALLOC(st->beta, sizeof(double));
     st->nprim = 1024;
     ALLOC(st->ppart, 2 * st->nprim * sizeof(double));
-    st->nbx = degrid_items_max(p);   // slots l * nbx + k; slots without a work item stay 0
-    ALLOC(st->dpart, (size_t)L * st->nbx * sizeof(double));
+    st->nbx = degrid_items_max(p);   // slots block * nbx + k; slots without a work item stay 0
+    ALLOC(st->dpart, (size_t)nb * st->nbx * sizeof(double));
+    ALLOC(st->rpart, (size_t)nb * st->nbx * sizeof(double));
     ALLOC(st->warm, (size_t)MAX_L_NUC * MAX_L_NUC * sizeof(float));
     ALLOC(st->sv, (size_t)std::max(L, 1) * sizeof(double));
     ALLOC(st->sv_rw, (size_t)std::max(L, 1) * sizeof(double));
@@ -462,12 +484,20 @@ hs_status hs_pd_state_create(hs_plan_t plan, const void* Y, const double* eps,
     HS_TRY(cu(cudaMemsetAsync(st->A, 0, NB * L * N * rs, s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->At, 0, L * N * rs, s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->v, 0, std::max<int64_t>(M, 1) * cs, s), "memset"));
-    HS_TRY(cu(cudaMemsetAsync(st->beta, 0, sizeof(double), s), "memset"));
-    HS_TRY(cu(cudaMemsetAsync(st->rho, 0, L * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->rho, 0, nb * sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->sv, 0, L * sizeof(double), s), "memset"));
     HS_TRY(cu(cudaMemsetAsync(st->nact, 0, sizeof(int), s), "memset"));
-    HS_TRY(cu(cudaMemsetAsync(st->dpart, 0, (size_t)L * st->nbx * sizeof(double), s), "memset"));
-    HS_TRY(cu(cudaMemcpyAsync(st->eps, eps, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "eps"));
+    HS_TRY(cu(cudaMemsetAsync(st->dpart, 0, (size_t)nb * st->nbx * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->rpart, 0, (size_t)nb * st->nbx * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->theta, 0, nb * sizeof(int64_t), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->resid, 0, nb * sizeof(double), s), "memset"));
+    HS_TRY(cu(cudaMemsetAsync(st->tcnt, 0, sizeof(int64_t), s), "memset"));
+    {   // beta^{(0)} undefined: +inf, so the first iteration never adjusts a bound
+        static const double inf = INFINITY;
+        HS_TRY(cu(cudaMemcpyAsync(st->beta, &inf, sizeof(double), cudaMemcpyHostToDevice, s), "beta"));
+        HS_TRY(cu(cudaStreamSynchronize(s), "beta"));
+    }
+    HS_TRY(cu(cudaMemcpyAsync(st->eps, eps, nb * sizeof(double), cudaMemcpyDeviceToDevice, s), "eps"));
     if (L <= MAX_L_NUC) {   // warm start of the eigensolver: identity
         std::vector<float> eye((size_t)L * L, 0.f);
         for (int i = 0; i < L; ++i) eye[(size_t)i * L + i] = 1.f;
@@ -499,7 +529,7 @@ hs_status hs_pd_set_data(hs_pd_state_t st, const void* Y, const double* eps, voi
     Plan* p = st->p;
     cudaStream_t s = S(stream);
     const int64_t M = p->M_total;
-    HS_CHECK_CUDA(cudaMemcpyAsync(st->eps, eps, p->g.L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HS_CHECK_CUDA(cudaMemcpyAsync(st->eps, eps, p->nblk * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (M > 0) {
         const unsigned g = (unsigned)std::min<int64_t>((M + 255) / 256, 8192);
         if (p->prec == HS_F32) k_gather_c2<<<g, 256, 0, s>>>((const float2*)Y, p->perm, (float2*)st->y, M);
@@ -553,8 +583,23 @@ static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
         da.y = st->y;
         da.d = st->d;
         da.part = st->dpart;
+        da.rpart = st->adapt.enable ? st->rpart : nullptr;
         HS_TRY(degrid(p, da, s));                                  // step 10 (+ residual norms)
         HS_TRY(ball_scale_from_partials(p, st->dpart, st->nbx, st->eps, st->rho, st->scale, s));
+        if (st->adapt.enable) {   // steps 13-19: bounds for the next iteration
+            AdaptArgs aa{};
+            aa.rpart = st->rpart;
+            aa.eps = st->eps;
+            aa.theta = st->theta;
+            aa.t = st->tcnt;
+            aa.beta = st->beta;
+            aa.resid = st->resid;
+            aa.lambda1 = st->adapt.lambda1;
+            aa.lambda2 = st->adapt.lambda2;
+            aa.lambda3 = st->adapt.lambda3;
+            aa.min_gap = st->adapt.min_gap;
+            HS_TRY(adapt_bounds(p->nblk, st->nbx, aa, s));
+        }
         GridArgs ga{};
         ga.mode = GIN_PD;
         ga.d = st->d;
@@ -570,7 +615,7 @@ static hs_status pd_step_launch(hs_pd_state* st, cudaStream_t s) {
     // ---- steps 20-23
     HS_TRY(primal_update(p, n, st->P, st->At, st->D, q.kappa1, q.kappa2, q.kappa3, q.tau,
                          q.use_nuclear, q.use_l21, st->X, st->Xt, st->ppart, st->nprim, s));
-    HS_TRY(beta_from_partials(st->ppart, st->nprim, st->beta, s));
+    HS_TRY(beta_from_partials(st->ppart, st->nprim, st->beta, st->tcnt, s));
     return HS_OK;
 }
 
@@ -624,7 +669,7 @@ hs_status hs_pd_get(hs_pd_state_t st, void* X, double* beta_host, double* rho_ho
     if (X) HS_CHECK_CUDA(cudaMemcpyAsync(X, st->X, (size_t)p->g.L * p->N() * p->rsize(),
                                          cudaMemcpyDeviceToDevice, s));
     if (beta_host) HS_CHECK_CUDA(cudaMemcpyAsync(beta_host, st->beta, sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (rho_host) HS_CHECK_CUDA(cudaMemcpyAsync(rho_host, st->rho, sizeof(double) * p->g.L,
+    if (rho_host) HS_CHECK_CUDA(cudaMemcpyAsync(rho_host, st->rho, sizeof(double) * p->nblk,
                                                 cudaMemcpyDeviceToHost, s));
     if (beta_host || rho_host) HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
@@ -686,6 +731,42 @@ hs_status hs_pd_reweight(hs_pd_state_t st, double gamma_l21, double gamma_nuc, v
         HS_TRY(nuclear_svals(p, st->X, sv, s));
         if (w_nuc) HS_TRY(reweight_sv(sv, p->g.L, gamma_nuc, w_nuc, s));
     }
+    return HS_OK;
+}
+
+hs_status hs_pd_set_adaptive(hs_pd_state_t st, const hs_adapt_params* a) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_set_adaptive: state is null");
+    hs_adapt_params q{};
+    if (a != nullptr && a->enable) {
+        if (!(a->lambda1 >= 0.0) || !(a->lambda2 >= 0.0) || !(a->lambda3 > 0.0 && a->lambda3 <= 1.0) ||
+            a->min_gap < 0)
+            return fail(HS_ERR_ARG, "hs_pd_set_adaptive: need lambda1, lambda2 >= 0, 0 < lambda3 <= 1, min_gap >= 0");
+        q = *a;
+    }
+    st->adapt = q;
+    if (st->gexec) {   // the captured iteration changes: capture again at the next graph solve
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+    }
+    if (st->graph) {
+        cudaGraphDestroy(st->graph);
+        st->graph = nullptr;
+    }
+    return HS_OK;
+}
+
+hs_status hs_pd_bounds(hs_pd_state_t st, double* eps_host, double* resid_host, int64_t* theta_host, void* stream) {
+    clear_error();
+    if (st == nullptr) return fail(HS_ERR_ARG, "hs_pd_bounds: state is null");
+    cudaStream_t s = S(stream);
+    const int nb = st->p->nblk;
+    if (eps_host) HS_CHECK_CUDA(cudaMemcpyAsync(eps_host, st->eps, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (resid_host)
+        HS_CHECK_CUDA(cudaMemcpyAsync(resid_host, st->resid, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (theta_host)
+        HS_CHECK_CUDA(cudaMemcpyAsync(theta_host, st->theta, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
 }
 

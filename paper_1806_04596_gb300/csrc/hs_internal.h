@@ -81,6 +81,10 @@ struct Plan {
     int64_t M_total = 0;
     int Mmax = 0;
     std::vector<int64_t> off_h;
+    std::vector<int64_t> blk_off_h;    // data blocks (caller = sorted boundaries), nblk + 1
+    std::vector<int> blk_ch;           // channel of every block
+    int nblk = 0;
+    int* blk_id = nullptr;             // block of every sorted visibility (only when nblk != L)
     int64_t* off_d = nullptr;          // L+1
     int* perm = nullptr;               // sorted index -> caller index
     void* coords = nullptr;            // FP32: uint2 fixed point; FP64: Coord64
@@ -154,7 +158,8 @@ struct DegridArgs {
     void* v;                // DOUT_PD: dual v (read), sorted
     const void* y;          // DOUT_PD: data, sorted
     void* d;                // DOUT_PD: output d = U^{-1/2} vbar - y, sorted
-    double* part;           // DOUT_PD: per-CTA partial ||d||^2, [L][blocks_x]
+    double* part;           // DOUT_PD: per-item partial ||d||^2, [blocks][items_max]
+    double* rpart;          // DOUT_PD: per-item partial ||y - Phi x~||^2, same layout, or null
 };
 hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s);
 int degrid_blocks_x(const Plan* p);   // chunks of DEGRID_CHUNK per channel (l2-ball partials)
@@ -164,12 +169,23 @@ struct GridArgs {
     int mode;
     const void* in;         // GIN_CALLER / GIN_SORTED: visibilities
     const void* d;          // GIN_PD: d from the de-gridding pass
-    const void* scale;      // GIN_PD: per-channel real factor max(0, 1 - eps / rho)
+    const void* scale;      // GIN_PD: per-block real factor max(0, 1 - eps / rho)
     void* v;                // GIN_PD: dual output v (home tile writes), sorted
 };
 hs_status grid(Plan* p, const GridArgs& a, cudaStream_t s);
 
 // l2-ball helpers (hs_prox.cu)
+struct AdaptArgs {          // Algorithm 2 steps 13-19 on the device
+    const double* rpart;    // per-item residual partials, [nblk][nparts]
+    double* eps;            // bounds (updated in place for the next iteration)
+    int64_t* theta;         // iteration of each block's last update
+    const int64_t* t;       // completed iterations (this one is t + 1)
+    const double* beta;     // beta of the previous iteration
+    double* resid;          // out: ||y_b - Phi_b x~||
+    double lambda1, lambda2, lambda3;
+    int64_t min_gap;
+};
+hs_status adapt_bounds(int nblk, int nparts, const AdaptArgs& a, cudaStream_t s);
 hs_status ball_scale_from_partials(Plan* p, const double* part, int nparts, const double* eps,
                                    double* rho, void* scale_real, cudaStream_t s);
 
@@ -201,7 +217,7 @@ hs_status ball_project(Plan* p, const void* Z, const void* Yd, const double* eps
 hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const void* D,
                         double k1, double k2, double k3, double tau, int use_p, int use_a,
                         void* X, void* Xt, double* part, int nparts, cudaStream_t s);
-hs_status beta_from_partials(const double* part, int nparts, double* beta, cudaStream_t s);
+hs_status beta_from_partials(const double* part, int nparts, double* beta, int64_t* t_count, cudaStream_t s);
 hs_status channel_norms(Plan* p, const void* X, double* out_dev, cudaStream_t s);
 hs_status scale_channels(Plan* p, void* X, const double* norms, cudaStream_t s);
 

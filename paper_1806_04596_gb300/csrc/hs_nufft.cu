@@ -71,6 +71,8 @@ template <typename R> struct NufftK {
     const R* scale;
     const int64_t* tile_off;
     const int* tile_ent;
+    const int* blk;    // block of every sorted visibility (data blocks), or null: one block per channel
+    double* rpart;     // DOUT_PD: per-item partial ||y - Phi x~||^2 (adaptive bounds), or null
 };
 
 // ---------------------------------------------------------------- de-gridding
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __res
     for (int k = 0; k < NC; ++k) c[k] = a.kbc[(7 - j) * NC + k];
     const int64_t beg = it.e0, end = it.e1;
     R sq = 0;   // this thread's share of ||d||^2 (few terms; FP64 only for the block sum)
+    R rq = 0;   // and of ||y - Phi x~||^2 (adaptive bounds)
     // lane j of a group preloads the coordinates of the group's j-th visibility
     int pcx = 0, pcy = 0;
     R pfx = 0, pfy = 0;
@@ -201,12 +204,20 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __res
                 }
                 a.d[i] = dd;
                 sq = fma(dd.x, dd.x, fma(dd.y, dd.y, sq));
+                if (a.rpart) {
+                    const CT r = csub(a.y[i], v);
+                    rq = fma(r.x, r.x, fma(r.y, r.y, rq));
+                }
             }
         }
     }
     if (MODE == DOUT_PD) {
         const double tot = block_sum((double)sq, red);
         if (threadIdx.x == 0) a.part[it.slot] = tot;
+        if (a.rpart) {
+            const double rt = block_sum((double)rq, red);
+            if (threadIdx.x == 0) a.rpart[it.slot] = rt;
+        }
     }
 }
 
@@ -276,7 +287,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
             } else if (MODE == GIN_SORTED) {
                 val = a.in[i];
             } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
-                val = cscale(a.d[i], a.scale[l]);
+                val = cscale(a.d[i], a.scale[a.blk ? a.blk[i] : l]);
                 if (a.u) val = cscale(val, sqrt(a.u[i]));
                 if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
             }
@@ -419,7 +430,7 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
                 } else if (MODE == GIN_SORTED) {
                     val = a.in[i];
                 } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the home tile stores it
-                    val = cscale(a.d[i], a.scale[l]);
+                    val = cscale(a.d[i], a.scale[a.blk ? a.blk[i] : l]);
                     if (a.u) val = cscale(val, sqrt(a.u[i]));
                     if ((k0x / TX == txi) && (k0y / TY == tyi)) a.v[i] = val;
                 }
@@ -523,6 +534,7 @@ template <typename R> static NufftK<R> base_args(Plan* p) {
     k.kbc = (const R*)p->kbc;
     k.tile_off = p->tile_off;
     k.tile_ent = p->tile_ent;
+    k.blk = p->blk_id;
     k.nblk_x = degrid_blocks_x(p);
     return k;
 }
@@ -535,6 +547,7 @@ static hs_status degrid_t(Plan* p, const DegridArgs& da, cudaStream_t s) {
     k.y = (const Cx<R>*)da.y;
     k.d = (Cx<R>*)da.d;
     k.part = da.part;
+    k.rpart = da.rpart;
     if (p->n_dg_items == 0) return HS_OK;
     const unsigned nb = (unsigned)p->n_dg_items;
     const size_t sm = (size_t)DG_REG * DG_LDS * sizeof(Cx<R>);

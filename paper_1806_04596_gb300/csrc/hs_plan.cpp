@@ -84,8 +84,8 @@ static hs_status download_real(const Plan* p, const void* src, int64_t n, std::v
     return HS_OK;
 }
 
-static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, const void* weights,
-                       const void* precond, cudaStream_t s) {
+static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const int64_t* block_offsets,
+                       const void* uv, const void* weights, const void* precond, cudaStream_t s) {
     Geo& g = p->g;
     const int L = g.L;
     p->off_h.assign(vis_offsets, vis_offsets + L + 1);
@@ -101,6 +101,27 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
     if (M > 0 && uv == nullptr) return fail(HS_ERR_ARG, "uv is null");
     p->M_total = M;
     p->Mmax = (int)Mmax;
+    // data blocks (Sec. 2.1, M_l^b): contiguous caller ranges inside channels
+    if (block_offsets == nullptr) {
+        p->blk_off_h = p->off_h;
+    } else {
+        if (nblocks < L) return fail(HS_ERR_ARG, "nblocks (%d) must be >= L (%d)", nblocks, L);
+        p->blk_off_h.assign(block_offsets, block_offsets + nblocks + 1);
+        if (p->blk_off_h[0] != 0 || p->blk_off_h[nblocks] != M)
+            return fail(HS_ERR_ARG, "block_offsets must run from 0 to the total visibility count");
+        for (int k = 0; k < nblocks; ++k)
+            if (p->blk_off_h[k + 1] < p->blk_off_h[k]) return fail(HS_ERR_ARG, "block_offsets must be nondecreasing");
+        for (int l = 1; l < L; ++l)   // every channel boundary must be a block boundary
+            if (!std::binary_search(p->blk_off_h.begin(), p->blk_off_h.end(), p->off_h[l]))
+                return fail(HS_ERR_ARG, "block_offsets must contain every channel boundary (channel %d)", l);
+    }
+    p->nblk = (int)p->blk_off_h.size() - 1;
+    p->blk_ch.assign(p->nblk, 0);
+    for (int k = 0; k < p->nblk; ++k) {   // channel of a block: the last channel starting at or before it
+        const int64_t x = p->blk_off_h[k];
+        const int l = (int)(std::upper_bound(p->off_h.begin(), p->off_h.end() - 1, x) - p->off_h.begin()) - 1;
+        p->blk_ch[k] = std::max(0, std::min(L - 1, l));
+    }
 
     std::vector<double> uvh, wh, uh;
     HS_TRY(download_real(p, uv, 2 * M, uvh, s));
@@ -128,11 +149,11 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
         cellx[i] = (int)((((int64_t)flu % Kx) + Kx) % Kx);
         celly[i] = (int)((((int64_t)flv % Ky) + Ky) % Ky);
     }
-    // sort each channel by (tile of the window start, cell)
+    // sort each block (each channel without blocks) by (tile of the window start, cell)
     std::vector<int> perm(M);
     std::vector<uint64_t> keys;
-    for (int l = 0; l < L; ++l) {
-        const int64_t a = p->off_h[l], b = p->off_h[l + 1];
+    for (int kb = 0; kb < p->nblk; ++kb) {
+        const int64_t a = p->blk_off_h[kb], b = p->blk_off_h[kb + 1];
         keys.resize(b - a);
         for (int64_t i = a; i < b; ++i) {
             const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
@@ -144,15 +165,23 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
         for (int64_t r = 0; r < b - a; ++r) perm[a + r] = (int)(a + (int64_t)(keys[r] & 0xffffffffu));
     }
     HS_TRY(upload(p, (void**)&p->perm, perm));
-    // de-gridding work items: runs of one window-start tile in each channel's
+    if (p->nblk != L) {   // block of every sorted visibility (gridding scale lookup)
+        std::vector<int> bid(M);
+        for (int kb = 0; kb < p->nblk; ++kb)
+            for (int64_t r = p->blk_off_h[kb]; r < p->blk_off_h[kb + 1]; ++r) bid[r] = kb;
+        HS_TRY(upload(p, (void**)&p->blk_id, bid));
+    }
+    // de-gridding work items: runs of one window-start tile in each block's
     // sorted range (cells before the fixed-point carry, as in the sort key), split
-    // into chunks of at most DEGRID_CHUNK visibilities; slot = l * items_max + k
+    // into chunks of at most DEGRID_CHUNK visibilities; slot = block * items_max + k
     {
         std::vector<int> items;
-        std::vector<int> per_l(L, 0);
+        const int nb = p->nblk;
+        std::vector<int> per_b(nb, 0);
         const int64_t ntl = (int64_t)g.ntx * g.nty;
-        for (int l = 0; l < L; ++l) {
-            const int64_t a = p->off_h[l], b = p->off_h[l + 1];
+        for (int kb = 0; kb < nb; ++kb) {
+            const int l = p->blk_ch[kb];
+            const int64_t a = p->blk_off_h[kb], b = p->blk_off_h[kb + 1];
             int64_t r = a;
             while (r < b) {
                 auto tile_of = [&](int64_t rr) {
@@ -165,16 +194,18 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
                 while (e < b && tile_of(e) == t) ++e;
                 for (int64_t c0 = r; c0 < e; c0 += DEGRID_CHUNK) {
                     const int64_t c1 = std::min<int64_t>(e, c0 + DEGRID_CHUNK);
-                    items.insert(items.end(), {(int)(l * ntl + t), (int)c0, (int)c1, per_l[l]++});
+                    items.insert(items.end(), {(int)(l * ntl + t), (int)c0, (int)c1, kb});
+                    ++per_b[kb];
                 }
                 r = e;
             }
         }
         int mx = 1;
-        for (int l = 0; l < L; ++l) mx = std::max(mx, per_l[l]);
-        for (size_t k = 0; k < items.size(); k += 4) {
-            const int l = (int)(items[k] / ntl);
-            items[k + 3] += l * mx;
+        for (int kb = 0; kb < nb; ++kb) mx = std::max(mx, per_b[kb]);
+        std::vector<int> seen(nb, 0);
+        for (size_t k = 0; k < items.size(); k += 4) {   // slot = block * items_max + rank in block
+            const int kb = items[k + 3];
+            items[k + 3] = kb * mx + seen[kb]++;
         }
         p->dg_items_max = mx;
         p->n_dg_items = (int64_t)items.size() / 4;
@@ -403,9 +434,10 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, const void* uv, cons
     return HS_OK;
 }
 
-hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, const void* uv,
-                      const void* weights, const void* precond, int oversample, int J, double kb_beta,
-                      int levels, hs_prec prec, unsigned flags, cudaStream_t s) {
+hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offsets, int nblocks,
+                      const int64_t* block_offsets, const void* uv, const void* weights, const void* precond,
+                      int oversample, int J, double kb_beta, int levels, hs_prec prec, unsigned flags,
+                      cudaStream_t s) {
     if (out == nullptr) return fail(HS_ERR_ARG, "out is null");
     *out = nullptr;
     if (vis_offsets == nullptr) return fail(HS_ERR_ARG, "vis_offsets is null");
@@ -445,7 +477,7 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
     g.ty = std::min(GRID_TILE, g.Ky);
     g.ntx = g.Kx / g.tx;
     g.nty = g.Ky / g.ty;
-    hs_status st = build(p.get(), vis_offsets, uv, weights, precond, s);
+    hs_status st = build(p.get(), vis_offsets, nblocks, block_offsets, uv, weights, precond, s);
     if (st != HS_OK) {
         plan_free(p.get());
         return st;

@@ -225,12 +225,41 @@ __global__ void k_ball_apply(const Cx<R>* __restrict__ Z, const Cx<R>* __restric
     }
 }
 
+// One CTA per data block of the plan (p->nblk; one per channel without blocks).
 hs_status ball_scale_from_partials(Plan* p, const double* part, int nparts, const double* eps,
                                    double* rho, void* scale_real, cudaStream_t s) {
     if (p->prec == HS_F32)
-        k_ball_scale<float><<<p->g.L, 256, 0, s>>>(part, nparts, eps, rho, (float*)scale_real);
+        k_ball_scale<float><<<p->nblk, 256, 0, s>>>(part, nparts, eps, rho, (float*)scale_real);
     else
-        k_ball_scale<double><<<p->g.L, 256, 0, s>>>(part, nparts, eps, rho, (double*)scale_real);
+        k_ball_scale<double><<<p->nblk, 256, 0, s>>>(part, nparts, eps, rho, (double*)scale_real);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+// Algorithm 2 steps 13-19, one CTA per block: rho_b = ||y_b - Phi_b x~|| from
+// the de-gridding partials; when beta^{(t-1)} < lambda_1, t - vartheta_b >
+// vartheta_bar and |rho_b - eps_b| / eps_b > lambda_2, eps_b <- lambda_3 rho_b
+// + (1 - lambda_3) eps_b and vartheta_b <- t (t = completed iterations + 1).
+__global__ void k_adapt(int nparts, AdaptArgs a) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) s += a.rpart[(int64_t)b * nparts + k];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        const double rho = sqrt(s);
+        a.resid[b] = rho;
+        const int64_t t = *a.t + 1;
+        const double e = a.eps[b];
+        if (*a.beta < a.lambda1 && t - a.theta[b] > a.min_gap && fabs(rho - e) / e > a.lambda2) {
+            a.eps[b] = a.lambda3 * rho + (1.0 - a.lambda3) * e;
+            a.theta[b] = t;
+        }
+    }
+}
+
+hs_status adapt_bounds(int nblk, int nparts, const AdaptArgs& a, cudaStream_t s) {
+    k_adapt<<<nblk, 128, 0, s>>>(nparts, a);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
@@ -608,7 +637,8 @@ __global__ void k_primal(int64_t n, const R* __restrict__ P, const R* __restrict
     }
 }
 
-__global__ void k_beta(const double* __restrict__ part, int nb, double* __restrict__ beta) {
+__global__ void k_beta(const double* __restrict__ part, int nb, double* __restrict__ beta,
+                       int64_t* __restrict__ t_count) {
     __shared__ double red[32];
     double dd = 0.0, xx = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -617,7 +647,10 @@ __global__ void k_beta(const double* __restrict__ part, int nb, double* __restri
     }
     dd = block_sum(dd, red);
     xx = block_sum(xx, red);
-    if (threadIdx.x == 0) *beta = (xx > 0.0) ? sqrt(dd / xx) : INFINITY;
+    if (threadIdx.x == 0) {
+        *beta = (xx > 0.0) ? sqrt(dd / xx) : INFINITY;
+        if (t_count) *t_count += 1;   // completed iterations (adaptive bounds)
+    }
 }
 
 hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const void* D,
@@ -637,8 +670,8 @@ hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const
     return HS_OK;
 }
 
-hs_status beta_from_partials(const double* part, int nparts, double* beta, cudaStream_t s) {
-    k_beta<<<1, 256, 0, s>>>(part, nparts, beta);
+hs_status beta_from_partials(const double* part, int nparts, double* beta, int64_t* t_count, cudaStream_t s) {
+    k_beta<<<1, 256, 0, s>>>(part, nparts, beta, t_count);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }

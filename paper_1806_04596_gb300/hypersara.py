@@ -39,7 +39,12 @@ class PlanInfo(C.Structure):
                 ("total_vis", C.c_int64), ("grid_tile_entries", C.c_int64),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("kb_terms", C.c_int),
                 ("kb_beta", C.c_double), ("kb_fit_max_err", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("nblocks", C.c_int)]
+
+
+class AdaptParams(C.Structure):
+    _fields_ = [("enable", C.c_int), ("lambda1", C.c_double), ("lambda2", C.c_double),
+                ("lambda3", C.c_double), ("min_gap", C.c_int64)]
 
 
 class PDParams(C.Structure):
@@ -55,6 +60,11 @@ _SIGS = {
     "hs_last_error": ([], C.c_char_p),
     "hs_plan_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64), _P, _P,
                         _P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_uint, _P], C.c_int),
+    "hs_plan_create_blocks": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_int,
+                               C.POINTER(C.c_int64), _P, _P, _P, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                               C.c_uint, _P], C.c_int),
+    "hs_pd_set_adaptive": ([_P, C.POINTER(AdaptParams)], C.c_int),
+    "hs_pd_bounds": ([_P, _P, _P, _P, _P], C.c_int),
     "hs_plan_destroy": ([_P], C.c_int),
     "hs_plan_info": ([_P, C.POINTER(PlanInfo)], C.c_int),
     "hs_phi_fwd": ([_P, _P, _P, _P], C.c_int),
@@ -155,7 +165,9 @@ class Plan:
 
     def __init__(self, nx: int, ny: int, offsets: Sequence[int], uv, weights=None, precond=None,
                  oversample: int = 2, J: int = 8, kb_beta: float = 0.0, levels: int = 4,
-                 prec: str = "f32", compensated: bool = False):
+                 prec: str = "f32", compensated: bool = False, blocks=None):
+        """blocks: optional offsets (caller order) of intra-channel data blocks, containing
+        every channel boundary (hs_plan_create_blocks)."""
         torch = _torch()
         lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -170,12 +182,24 @@ class Plan:
                 raise ValueError(f"{name} must have dtype {self.rdtype}")
         self._keep = (uv, weights, precond)
         h = C.c_void_p()
-        st = lib.hs_plan_create(C.byref(h), self.nx, self.ny, self.L,
-                                off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
-                                _ptr(precond), oversample, J, float(kb_beta), levels,
-                                HS_F32 if prec == "f32" else HS_F64,
-                                HS_PLAN_COMPENSATED if compensated else 0, _stream())
+        if blocks is None:
+            self.blocks = off
+            st = lib.hs_plan_create(C.byref(h), self.nx, self.ny, self.L,
+                                    off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
+                                    _ptr(precond), oversample, J, float(kb_beta), levels,
+                                    HS_F32 if prec == "f32" else HS_F64,
+                                    HS_PLAN_COMPENSATED if compensated else 0, _stream())
+        else:
+            bo = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64))
+            self.blocks = bo
+            st = lib.hs_plan_create_blocks(C.byref(h), self.nx, self.ny, self.L,
+                                           off.ctypes.data_as(C.POINTER(C.c_int64)), len(bo) - 1,
+                                           bo.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
+                                           _ptr(precond), oversample, J, float(kb_beta), levels,
+                                           HS_F32 if prec == "f32" else HS_F64,
+                                           HS_PLAN_COMPENSATED if compensated else 0, _stream())
         _check("hs_plan_create", st)
+        self.nblocks = len(self.blocks) - 1
         self.h = h
         self._keep = None
         self.M = int(off[-1])
@@ -307,7 +331,7 @@ class PDState:
         """Returns (X copy, beta, rho per channel as numpy)."""
         X = self.plan.cube() if X is None else X
         beta = C.c_double()
-        rho = (C.c_double * self.plan.L)()
+        rho = (C.c_double * self.plan.nblocks)()
         _check("hs_pd_get", load().hs_pd_get(self.h, _ptr(X), C.byref(beta), rho, _stream()))
         return X, beta.value, np.array(rho[:])
 
@@ -317,6 +341,19 @@ class PDState:
         n = C.c_int()
         _check("hs_pd_nuclear_info", load().hs_pd_nuclear_info(self.h, sv, C.byref(n), _stream()))
         return np.array(sv[:]), n.value
+
+    def set_adaptive(self, enable: bool = True, lambda1: float = 5e-4, lambda2: float = 0.01,
+                     lambda3: float = 0.618, min_gap: int = 100):
+        """Adaptive l2 bounds (Algorithm 2 steps 13-19); the paper's defaults."""
+        prm = AdaptParams(int(enable), lambda1, lambda2, lambda3, int(min_gap))
+        _check("hs_pd_set_adaptive", load().hs_pd_set_adaptive(self.h, C.byref(prm)))
+
+    def bounds(self):
+        """(eps, last residuals ||y_b - Phi_b x~||, vartheta) per data block, numpy."""
+        nb = self.plan.nblocks
+        e, r, t = (C.c_double * nb)(), (C.c_double * nb)(), (C.c_int64 * nb)()
+        _check("hs_pd_bounds", load().hs_pd_bounds(self.h, e, r, t, _stream()))
+        return np.array(e[:]), np.array(r[:]), np.array(t[:])
 
     def reweight(self, gamma_l21: float, gamma_nuc: float, w_l21=None, w_nuc=None, sv=None):
         """hs_pd_reweight: Algorithm 1 weights from the current X into w_l21 (9 x ny x nx,
