@@ -9,7 +9,8 @@
 //
 //  1. FP32 cyclic Jacobi (round-robin parallel ordering) on S, warm-started
 //     from the previous call's eigenvectors V0 (A = V0^T S V0), gives every
-//     eigenpair to FP32 accuracy.
+//     eigenpair to FP32 accuracy; warm calls skip it while V0 still
+//     diagonalises S to 2e-5 (late in a solve, when S changes slowly).
 //  2. The active eigenvectors are refined in FP64 against the rest of the
 //     basis with first-order correction steps (one from a warm basis, two
 //     cold) of an approximate eigendecomposition (Ogita & Aishima 2018): with
@@ -83,7 +84,7 @@ __device__ __forceinline__ void jac_rot(double app, double aqq, double apq, doub
 // sweeps stop when the off-diagonal Frobenius norm is at most off_rel ||A||_F,
 // when a sweep applies no rotation, or after max_sweeps.
 template <typename T, int N>
-__device__ void jacobi_blocks(T* A, T* V, const unsigned short* pairs, double skip, double floor_rel,
+__device__ void jacobi_blocks(T* A, T* V, unsigned short* pairs, double skip, double floor_rel,
                               double off_rel, int max_sweeps, Cx<T>* cs, double* red, int* flag) {
     constexpr int LDJ = MAX_L_NUC + 1;
     constexpr int NP = N / 2;
@@ -102,6 +103,10 @@ __device__ void jacobi_blocks(T* A, T* V, const unsigned short* pairs, double sk
         const double nrm = eig_bsum((double)nrmT, red);
         const double off = eig_bsum((double)offT, red);
         if (!(off > off_rel * off_rel * nrm)) break;
+        if (sweep == 0) {   // the round-robin schedule, built only when a sweep runs
+            rr_schedule(N, pairs);
+            __syncthreads();
+        }
         const T flo = (T)(floor_rel * sqrt(nrm));
         if (tid == 0) *flag = 0;
         __syncthreads();
@@ -163,8 +168,6 @@ __device__ void jacobi_n(int n, T* A, T* B, T* V, T* W, unsigned short* pairs, d
                          double floor_rel, double off_rel, int max_sweeps, Cx<T>* cs, double* red, int* flag) {
     (void)B;
     (void)W;
-    rr_schedule(n, pairs);
-    __syncthreads();
 #define HS_JAC(NN) jacobi_blocks<T, NN>(A, V, pairs, skip, floor_rel, off_rel, max_sweeps, cs, red, flag)
     switch (n) {
         case 2: HS_JAC(2); break;
@@ -216,19 +219,40 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
         V32[i * LD32 + j] = (warm && i < L && j < L) ? warm[i * L + j] : (i == j ? 1.f : 0.f);
     }
     __syncthreads();
-    if (warm) {   // A = V0^T S V0 (FP32), then symmetrise
-        for (int k = tid; k < n * n; k += nt) {
-            const int i = k / n, j = k - i * n;
-            float acc = 0.f;
-            for (int m = 0; m < n; ++m) acc = fmaf(A32[i * LD32 + m], V32[m * LD32 + j], acc);
-            T32[i * LD32 + j] = acc;
+    if (warm) {   // A = V0^T S V0 (FP32), then symmetrise; 2 x 2 output blocks per thread
+        const int nh = n >> 1;
+        for (int k = tid; k < nh * nh; k += nt) {   // T = S V0
+            const int i = 2 * (k / nh), j = 2 * (k % nh);
+            float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+            for (int m = 0; m < n; ++m) {
+                const float s0 = A32[i * LD32 + m], s1 = A32[(i + 1) * LD32 + m];
+                const float v0 = V32[m * LD32 + j], v1 = V32[m * LD32 + j + 1];
+                a00 = fmaf(s0, v0, a00);
+                a01 = fmaf(s0, v1, a01);
+                a10 = fmaf(s1, v0, a10);
+                a11 = fmaf(s1, v1, a11);
+            }
+            T32[i * LD32 + j] = a00;
+            T32[i * LD32 + j + 1] = a01;
+            T32[(i + 1) * LD32 + j] = a10;
+            T32[(i + 1) * LD32 + j + 1] = a11;
         }
         __syncthreads();
-        for (int k = tid; k < n * n; k += nt) {
-            const int i = k / n, j = k - i * n;
-            float acc = 0.f;
-            for (int m = 0; m < n; ++m) acc = fmaf(V32[m * LD32 + i], T32[m * LD32 + j], acc);
-            A32[i * LD32 + j] = acc;
+        for (int k = tid; k < nh * nh; k += nt) {   // A = V0^T T
+            const int i = 2 * (k / nh), j = 2 * (k % nh);
+            float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+            for (int m = 0; m < n; ++m) {
+                const float u0 = V32[m * LD32 + i], u1 = V32[m * LD32 + i + 1];
+                const float t0 = T32[m * LD32 + j], t1 = T32[m * LD32 + j + 1];
+                a00 = fmaf(u0, t0, a00);
+                a01 = fmaf(u0, t1, a01);
+                a10 = fmaf(u1, t0, a10);
+                a11 = fmaf(u1, t1, a11);
+            }
+            A32[i * LD32 + j] = a00;
+            A32[i * LD32 + j + 1] = a01;
+            A32[(i + 1) * LD32 + j] = a10;
+            A32[(i + 1) * LD32 + j + 1] = a11;
         }
         __syncthreads();
         for (int k = tid; k < n * n; k += nt) {
@@ -242,9 +266,13 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
         __syncthreads();
     }
     // ---- 1. FP32 Jacobi on every eigenpair
-    // warm-started calls run one FP32 sweep: the active pairs are made exact in
-    // FP64 below, and the basis keeps improving from call to call
-    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, 2e-6, warm ? 1 : 15, cs32, red, &flag);
+    // warm-started calls run at most one FP32 sweep, and none while the previous
+    // basis still diagonalises S to 2e-5 (relative off-diagonal Frobenius norm,
+    // about twice the FP32 rounding of V0^T S V0): the active pairs are made exact in
+    // FP64 below from a basis that accurate, and the basis is swept again as
+    // soon as S has drifted further
+    jacobi_n<float>(n, A32, B32, V32, W32, partner, 1e-7, 2e-7, warm ? 2e-5 : 2e-6, warm ? 1 : 15, cs32, red,
+                    &flag);
     // ---- eigenvalues, descending order (rank by counting), warm start for the next call
     if (tid < L) {
         lamf[tid] = A32[tid * LD32 + tid];
