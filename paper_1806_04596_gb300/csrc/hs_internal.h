@@ -42,6 +42,15 @@ constexpr int GRID_TILE = 32;        // gridding tile side (cells)
 constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumulators)
 constexpr int GRID_CAP = 512;        // most list entries one gridding CTA processes
 constexpr int DEGRID_CHUNK = 256;    // visibilities per degridding CTA
+constexpr int SWEEP_HMAX = 64;       // most output rows of one sweep-gridding work item
+constexpr int SWEEP_CAP = 1024;      // windows above which a sweep item's rows are cut short
+
+// Sweep-gridding work item (grids of at least 64 x 64 cells): channel l, the
+// 32-column strip `strip`, output rows [row0, row1); list range [e0, e1) of
+// groups of 4 slots (see the plan builder).
+struct SweepItem {
+    int l, strip, row0, row1, e0, e1;
+};
 constexpr int MAX_L_NUC = 64;        // largest L for the nuclear-norm prox
 // Low-rank form of the nuclear prox factor M = base I + sum_c g_c x_c x_c^T
 // (doubles in Plan::eigf): [LR_R] active count r, [LR_BASE] 1 (dual) or 0,
@@ -102,6 +111,10 @@ struct Plan {
     void* grid_merges = nullptr;       // split tiles {tix, slot0, nslot}
     int64_t n_merges = 0;
     void* grid_partial = nullptr;      // partial tiles of split tiles (complex, slots x tile)
+    void* sw_items = nullptr;          // sweep-gridding work items (SweepItem), heaviest first
+    int64_t n_sw_items = 0;
+    int* sw_ent = nullptr;             // sweep lists: groups of 4 sorted visibility indices, -1 = padding
+    int64_t n_sw_ent = 0;
     void* kbc = nullptr;               // 8 * kb_terms reals
     void* cxs = nullptr;               // nx reals (Z scale along x)
     void* cys = nullptr;               // ny reals

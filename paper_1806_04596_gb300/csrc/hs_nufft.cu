@@ -12,15 +12,15 @@
 // shuffles. Visibilities are processed in the plan's tile-sorted order so
 // neighbouring lanes touch neighbouring grid cells.
 //
-// Gridding: one CTA per (channel, 32 x 32 output tile) consumes the tile's list
-// of visibilities whose window overlaps it (built by the plan) and writes every
-// output cell of the tile exactly once, so the grid needs no zeroing pass and
-// no global atomics. Every warp adds windows into its own private copy of the
-// tile in shared memory and the copies are combined in a fixed order, so the
-// result is deterministic. Default kernel: the plan groups each list into 4
-// mutually non-overlapping windows, which one warp adds at once (8 lanes per
-// window). HS_PLAN_COMPENSATED kernel: one window per warp at a time, with
-// Kahan-compensated FP32 sums.
+// Gridding writes every output cell exactly once, so the grid needs no zeroing
+// pass and no global atomics, and sums in a fixed order (deterministic).
+// Default kernel on grids of at least 64 x 64 cells: the register sweep
+// (k_grid_sweep, below). Smaller grids: one CTA per (channel, 32 x 32 tile)
+// consumes the tile's list of overlapping windows, every warp adding groups of
+// 4 mutually non-overlapping windows into its private copy of the tile in
+// shared memory, the copies combined in a fixed order. HS_PLAN_COMPENSATED
+// kernel: the same tiles, one window per warp at a time, with Kahan-compensated
+// FP32 sums.
 #include "hs_device.cuh"
 #include "hs_internal.h"
 
@@ -494,6 +494,142 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
     }
 }
 
+// Sweep gridding (grids of at least 64 x 64 cells, default kernel). A warp owns
+// one work item of the plan: a 32-column strip of one channel's grid and its
+// output rows [row0, row1). Lane c holds column c of two 8-row bands in
+// registers, A = rows 8j .. 8j + 7 and B = rows 8j + 8 .. 8j + 15 (relative to
+// row0), and walks the item's groups band by band: when a group of a later
+// band arrives, A is final, so it is stored (each output cell once, coalesced
+// 256-byte rows) and the bands move up (A = B, B = 0). A group holds up to 4
+// windows with disjoint columns starting in band j, so they all lie in A and B
+// and one pass over the 16 rows (2 x 16 FMAs per lane) adds them; no
+// shared-memory read-modify-write, no atomics, and a fixed summation order.
+// Lists are consumed in batches of 32 slots: lane q decodes slot q (coordinates,
+// weighted value, the 16 kernel taps) into shared memory, the row taps placed
+// at their rows of the 16-row window A, B (zeros elsewhere).
+constexpr int SW_WARPS = 4;      // warps (work items) per CTA
+constexpr int SW_LD = 28;        // staged reals per slot: 8 column taps, 16 row taps, value, pad
+constexpr int SW_PAD = 1 << 20;  // start column of a padding slot (covers no lane)
+
+// 4 consecutive reals from 16-byte aligned shared memory
+__device__ __forceinline__ void sw_ld4(const float* p, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void sw_ld4(const double* p, double* v) {
+    const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+}
+
+template <typename R, int NC, int MODE>
+__global__ void __launch_bounds__(SW_WARPS * 32) k_grid_sweep(NufftK<R> a, const SweepItem* __restrict__ items,
+                                                             const int* __restrict__ ent, int n_items) {
+    typedef Cx<R> CT;
+    __shared__ __align__(16) R stage[SW_WARPS][32 * SW_LD];
+    __shared__ __align__(16) int sxs[SW_WARPS][32];   // start column of every slot (relative to the strip)
+    __shared__ int sjb[SW_WARPS][8];                  // band of every group
+    __shared__ R skb[8 * NC];
+    for (int k = threadIdx.x; k < 8 * NC; k += blockDim.x) skb[k] = a.kbc[k];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wi = blockIdx.x * SW_WARPS + w;
+    if (wi >= n_items) return;
+    const SweepItem it = items[wi];
+    const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int c0 = it.strip * GRID_TILE, row0 = it.row0, H = it.row1 - it.row0;
+    CT* out = a.grid_out + (int64_t)it.l * Ky * Kx + (int64_t)row0 * Kx + c0 + lane;
+    R* st = stage[w];
+    CT A[8], B[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) A[k] = B[k] = cx<R>(0, 0);
+    int jb = -1;   // band held in A (rows -8 .. -1 are never stored)
+    // store band A (rows 8 jb .. 8 jb + 7 inside [0, H)), move B into A
+    auto advance = [&]() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = 8 * jb + k;
+            if ((unsigned)r < (unsigned)H) out[(int64_t)r * Kx] = A[k];
+            A[k] = B[k];
+            B[k] = cx<R>(0, 0);
+        }
+        ++jb;
+    };
+    for (int b0 = it.e0; b0 < it.e1; b0 += 32) {
+        // ---- decode slot b0 + lane
+        const int i = b0 + lane < it.e1 ? ent[b0 + lane] : -1;
+        int rx = SW_PAD, ry = 0;
+        if (i >= 0) {
+            int cxv, cyv;
+            R fx, fy;
+            VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
+            const int k0x = (cxv - 3) & (Kx - 1);
+            const int k0y = (cyv - 3) & (Ky - 1);
+            rx = ((k0x - c0 + 7) & (Kx - 1)) - 7;     // -7 .. 31
+            ry = ((k0y - row0 + 7) & (Ky - 1)) - 7;   // -7 .. H - 1
+            CT val;
+            if (MODE == GIN_CALLER) {
+                val = a.in[a.perm[i]];
+            } else if (MODE == GIN_SORTED) {
+                val = a.in[i];
+            } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the item holding the window start stores it
+                val = cscale(a.d[i], a.scale[a.blk ? a.blk[i] : it.l]);
+                if (a.u) val = cscale(val, sqrt(a.u[i]));
+                if (rx >= 0 && ry >= 0 && ry < H) a.v[i] = val;
+            }
+            if (a.w) val = cscale(val, a.w[i]);
+            const R su = (R)2 * fx - (R)1, sv = (R)2 * fy - (R)1;
+            R pu[8], pv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const R* cf = skb + (7 - m) * NC;
+                pu[m] = horner<R, NC>(cf, su);   // phi_u of window column m
+                pv[m] = horner<R, NC>(cf, sv);   // phi_v of window row m
+            }
+            R* sl = st + lane * SW_LD;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) sl[m] = pu[m];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) sl[8 + k] = (R)0;
+            R* sr = sl + 8 + (ry & 7);   // row m of the window is row (ry & 7) + m of A, B
+#pragma unroll
+            for (int m = 0; m < 8; ++m) sr[m] = pv[m];
+            sl[24] = val.x;
+            sl[25] = val.y;
+        }
+        sxs[w][lane] = rx;
+        if ((lane & 3) == 0) sjb[w][lane >> 2] = ry >> 3;
+        __syncwarp();
+        // ---- add the batch's groups
+        const int ng = min(8, (it.e1 - b0) >> 2);
+        for (int q = 0; q < ng; ++q) {
+            const int gj = sjb[w][q];
+            while (jb < gj) advance();
+            // the group's slots start in increasing columns and cover disjoint lanes
+            const int4 xs = reinterpret_cast<const int4*>(sxs[w])[q];
+            const int sel = (lane >= xs.y) + (lane >= xs.z) + (lane >= xs.w);
+            const int sx = sxs[w][4 * q + sel];
+            const int dx = lane - sx;
+            const R* sl = st + (4 * q + sel) * SW_LD;
+            const R pu = (unsigned)dx < 8u ? sl[dx] : (R)0;
+            R vv[4];
+            sw_ld4(sl + 24, vv);
+            const R pr = pu * vv[0], pi = pu * vv[1];
+            R pv[16];
+#pragma unroll
+            for (int k = 0; k < 16; k += 4) sw_ld4(sl + 8 + k, pv + k);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                A[k].x = fma(pv[k], pr, A[k].x);
+                A[k].y = fma(pv[k], pi, A[k].y);
+                B[k].x = fma(pv[8 + k], pr, B[k].x);
+                B[k].y = fma(pv[8 + k], pi, B[k].y);
+            }
+        }
+        __syncwarp();
+    }
+    while (8 * jb < H) advance();
+}
+
 // Sum of the partial tiles of every split tile (fixed slot order).
 struct GridMerge {
     int tix, slot0, nslot;
@@ -571,6 +707,13 @@ hs_status degrid(Plan* p, const DegridArgs& a, cudaStream_t s) {
 template <typename R, int NC, int MODE, bool KAHAN>
 static hs_status grid_launch(Plan* p, NufftK<R>& k, cudaStream_t s) {
     const size_t smem = (size_t)GRID_WARPS * p->g.tx * p->g.ty * sizeof(Cx<R>) * (KAHAN ? 2 : 1);
+    if (!KAHAN && p->n_sw_items > 0) {
+        const unsigned nb = (unsigned)((p->n_sw_items + SW_WARPS - 1) / SW_WARPS);
+        k_grid_sweep<R, NC, MODE><<<nb, SW_WARPS * 32, 0, s>>>(k, (const SweepItem*)p->sw_items, p->sw_ent,
+                                                             (int)p->n_sw_items);
+        HS_CHECK_LAUNCH();
+        return HS_OK;
+    }
     if (p->n_items == 0) return HS_OK;
     if (KAHAN)
         k_grid<R, NC, MODE, KAHAN><<<(unsigned)p->n_items, GRID_WARPS * 32, smem, s>>>(

@@ -8,9 +8,11 @@
 //  * a per-channel sort of the visibilities by the 32 x 32 grid tile holding
 //    the start of their 8 x 8 window, then by cell, so that consecutive
 //    visibilities touch neighbouring grid cells;
-//  * for every (channel, tile) the list of visibilities whose window overlaps
-//    the tile (a window straddles at most 2 x 2 tiles), which the gridding
-//    kernel consumes without atomics;
+//  * the gridding lists, consumed without atomics: for grids of at least
+//    64 x 64 cells, per (channel, 32-column strip, row range) the windows that
+//    reach it, grouped by start row into disjoint column ranges (sweep
+//    kernel); otherwise, and for the compensated kernel, per (channel, 32 x 32
+//    tile) the windows that overlap it (a window straddles at most 2 x 2 tiles);
 //  * the Kaiser-Bessel polynomial pieces, the Z scaling, the FFT twiddles;
 //  * all scratch buffers, so that no compute call allocates.
 #include <algorithm>
@@ -81,6 +83,103 @@ static hs_status download_real(const Plan* p, const void* src, int64_t n, std::v
         HS_CHECK_CUDA(cudaMemcpyAsync(out.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost, s));
         HS_CHECK_CUDA(cudaStreamSynchronize(s));
     }
+    return HS_OK;
+}
+
+// Gridding lists of the sweep kernel (grids of at least 64 x 64 cells). A work
+// item is one channel, one 32-column strip and its output rows [row0, row1);
+// its list holds every window that overlaps the strip and starts in rows
+// row0 - 7 .. row1 - 1 (circularly), as groups of 4 slots (-1 pads) whose
+// windows cover disjoint columns of the strip (slots in increasing start
+// column) and start in the same 8-row band (relative start row y, band
+// floor(y / 8)), so that they all lie in that band and the next. Windows are
+// placed in increasing start row, first fit over the band's groups; groups are
+// stored by band. Rows are cut after SWEEP_HMAX rows, or earlier once the list
+// would pass SWEEP_CAP windows (at least one row per item). Items are stored
+// heaviest first.
+static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::vector<int>& cellx,
+                             const std::vector<int>& celly) {
+    const Geo& g = p->g;
+    const int Kx = g.Kx, Ky = g.Ky, L = g.L;
+    const int nstrip = Kx / GRID_TILE;
+    const int hmax = std::min(SWEEP_HMAX, Ky - 8);
+    struct Win {
+        int y, x, r;   // start row (absolute, then relative to row0), start column relative to the strip
+    };
+    std::vector<std::vector<Win>> strips(nstrip);
+    std::vector<int64_t> rowcnt(Ky);
+    std::vector<Win> seg;
+    std::vector<SweepItem> items;
+    std::vector<int> ent;
+    struct Grp {
+        int y, m;        // band, windows held
+        uint32_t mask;   // strip columns covered
+        int e[4], x[4];  // sorted visibility indices and start columns, by start column
+    };
+    std::vector<Grp> open;
+    for (int l = 0; l < L; ++l) {
+        for (auto& v : strips) v.clear();
+        for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
+            const int64_t i = perm[r];
+            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+            const int s0 = k0x / GRID_TILE, s1 = ((k0x + 7) & (Kx - 1)) / GRID_TILE;
+            strips[s0].push_back({k0y, k0x - s0 * GRID_TILE, (int)r});
+            if (s1 != s0) strips[s1].push_back({k0y, ((k0x - s1 * GRID_TILE + 7) & (Kx - 1)) - 7, (int)r});
+        }
+        for (int st = 0; st < nstrip; ++st) {
+            const std::vector<Win>& ws = strips[st];
+            std::fill(rowcnt.begin(), rowcnt.end(), 0);
+            for (const Win& w : ws) ++rowcnt[w.y];
+            for (int row0 = 0; row0 < Ky;) {
+                int64_t cnt = 0;
+                for (int d = 1; d <= 7; ++d) cnt += rowcnt[(row0 - d) & (Ky - 1)];
+                int row1 = row0;
+                while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= SWEEP_CAP))
+                    cnt += rowcnt[row1++];
+                const int H = row1 - row0;
+                seg.clear();
+                for (const Win& w : ws) {
+                    const int ry = ((w.y - row0 + 7) & (Ky - 1)) - 7;
+                    if (ry < H) seg.push_back({ry, w.x, w.r});
+                }
+                std::sort(seg.begin(), seg.end(), [](const Win& a, const Win& b) {
+                    return a.y != b.y ? a.y < b.y : (a.x != b.x ? a.x < b.x : a.r < b.r);
+                });
+                const int e0 = (int)ent.size();
+                open.clear();
+                size_t first = 0;
+                for (const Win& w : seg) {
+                    const int b = std::max(w.x, 0), e = std::min(w.x + 8, GRID_TILE);
+                    const uint32_t mask = (uint32_t)(((uint64_t)1 << e) - ((uint64_t)1 << b));
+                    const int band = (w.y + 8) / 8 - 1;   // floor(y / 8), y >= -7
+                    while (first < open.size() && open[first].y < band) ++first;
+                    size_t gi = first;
+                    while (gi < open.size() && (open[gi].m == 4 || (open[gi].mask & mask))) ++gi;
+                    if (gi == open.size()) open.push_back({band, 0, 0u, {-1, -1, -1, -1}, {0, 0, 0, 0}});
+                    Grp& gr = open[gi];
+                    int k = gr.m++;   // keep the slots in increasing start column
+                    for (; k > 0 && gr.x[k - 1] > w.x; --k) {
+                        gr.e[k] = gr.e[k - 1];
+                        gr.x[k] = gr.x[k - 1];
+                    }
+                    gr.e[k] = w.r;
+                    gr.x[k] = w.x;
+                    gr.mask |= mask;
+                }
+                for (const Grp& gr : open) ent.insert(ent.end(), gr.e, gr.e + 4);
+                if (ent.size() >= ((size_t)1 << 31)) return fail(HS_ERR_ARG, "too many gridding list entries");
+                items.push_back({l, st, row0, row1, e0, (int)ent.size()});
+                row0 = row1;
+            }
+        }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const SweepItem& a, const SweepItem& b) {
+        return (a.e1 - a.e0) + 4 * (a.row1 - a.row0) > (b.e1 - b.e0) + 4 * (b.row1 - b.row0);
+    });
+    p->n_sw_items = (int64_t)items.size();
+    p->n_sw_ent = (int64_t)ent.size();
+    HS_TRY(upload(p, &p->sw_items, items));
+    HS_TRY(upload(p, (void**)&p->sw_ent, ent));
     return HS_OK;
 }
 
@@ -257,130 +356,137 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
                                  : upload_real<double>(p, &p->u_sorted, us));
     }
 
-    // gridding lists: every (channel, tile) overlapped by a window
-    const int64_t nt = p->ntiles();
-    std::vector<int64_t> toff((size_t)L * nt + 1, 0);
-    auto tiles_of = [&](int64_t r, int* txs, int* tys, int& ntx_, int& nty_) {
-        const int64_t i = perm[r];
-        const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
-        txs[0] = k0x / TX;
-        txs[1] = ((k0x + 7) & (Kx - 1)) / TX;
-        tys[0] = k0y / TY;
-        tys[1] = ((k0y + 7) & (Ky - 1)) / TY;
-        ntx_ = txs[1] != txs[0] ? 2 : 1;
-        nty_ = tys[1] != tys[0] ? 2 : 1;
-    };
-    for (int l = 0; l < L; ++l)
-        for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
-            int txs[2], tys[2], a, b;
-            tiles_of(r, txs, tys, a, b);
-            for (int yy = 0; yy < b; ++yy)
-                for (int xx = 0; xx < a; ++xx) ++toff[1 + (size_t)l * nt + tys[yy] * g.ntx + txs[xx]];
-        }
-    for (size_t k = 1; k < toff.size(); ++k) toff[k] += toff[k - 1];
-    if (toff.back() >= ((int64_t)1 << 30)) return fail(HS_ERR_ARG, "too many gridding list entries");
-    std::vector<int> ent((size_t)toff.back());
-    {
-        std::vector<int64_t> fill(toff.begin(), toff.end() - 1);
+    // gridding lists: the sweep kernel's for grids of at least 64 x 64 cells;
+    // per-tile lists for smaller grids and the compensated kernel
+    const bool sweep = Kx >= 2 * GRID_TILE && Ky >= 2 * GRID_TILE;
+    if (sweep) HS_TRY(build_sweep(p, perm, cellx, celly));
+    if (!sweep || (p->flags & HS_PLAN_COMPENSATED)) {
+        // gridding lists: every (channel, tile) overlapped by a window
+        const int64_t nt = p->ntiles();
+        std::vector<int64_t> toff((size_t)L * nt + 1, 0);
+        auto tiles_of = [&](int64_t r, int* txs, int* tys, int& ntx_, int& nty_) {
+            const int64_t i = perm[r];
+            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+            txs[0] = k0x / TX;
+            txs[1] = ((k0x + 7) & (Kx - 1)) / TX;
+            tys[0] = k0y / TY;
+            tys[1] = ((k0y + 7) & (Ky - 1)) / TY;
+            ntx_ = txs[1] != txs[0] ? 2 : 1;
+            nty_ = tys[1] != tys[0] ? 2 : 1;
+        };
         for (int l = 0; l < L; ++l)
             for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
                 int txs[2], tys[2], a, b;
                 tiles_of(r, txs, tys, a, b);
                 for (int yy = 0; yy < b; ++yy)
-                    for (int xx = 0; xx < a; ++xx)
-                        ent[fill[(size_t)l * nt + tys[yy] * g.ntx + txs[xx]]++] = (int)r;
+                    for (int xx = 0; xx < a; ++xx) ++toff[1 + (size_t)l * nt + tys[yy] * g.ntx + txs[xx]];
             }
-    }
-    // Regroup every list into groups of 4 entries whose windows do not overlap
-    // (circular distance >= 8 cells in x or y), padding with -1, so that the
-    // gridding kernel can add the 4 windows of a group at once without atomics.
-    // Greedy, in list order: an entry joins the first open group it fits; at
-    // most GROUP_OPEN groups are open, the oldest is closed (padded) to make room.
-    std::vector<int64_t> goff((size_t)L * nt + 1, 0);
-    std::vector<int> gent;
-    gent.reserve((size_t)(toff.back() + toff.back() / 4 + 64));
-    {
-        constexpr int GROUP_OPEN = 64;
-        struct Group {
-            int m;
-            int e[4], x[4], y[4];
-        };
-        auto circ = [](int d, int K) {
-            d &= K - 1;
-            return d < K - d ? d : K - d;
-        };
-        std::vector<Group> open;
-        auto emit = [&](const Group& g) {
-            for (int k = 0; k < 4; ++k) gent.push_back(k < g.m ? g.e[k] : -1);
-        };
-        for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
-            open.clear();
-            for (int64_t q = toff[tix]; q < toff[tix + 1]; ++q) {
-                const int r = ent[q];
-                const int64_t i = perm[r];
-                const int x = (cellx[i] - 3) & (Kx - 1), y = (celly[i] - 3) & (Ky - 1);
-                bool placed = false;
-                for (size_t gi = 0; gi < open.size() && !placed; ++gi) {
-                    Group& g = open[gi];
-                    bool fits = true;
-                    for (int k = 0; k < g.m && fits; ++k)
-                        fits = circ(x - g.x[k], Kx) >= 8 || circ(y - g.y[k], Ky) >= 8;
-                    if (!fits) continue;
-                    g.e[g.m] = r;
-                    g.x[g.m] = x;
-                    g.y[g.m] = y;
-                    if (++g.m == 4) {
-                        emit(g);
-                        open.erase(open.begin() + gi);
+        for (size_t k = 1; k < toff.size(); ++k) toff[k] += toff[k - 1];
+        if (toff.back() >= ((int64_t)1 << 30)) return fail(HS_ERR_ARG, "too many gridding list entries");
+        std::vector<int> ent((size_t)toff.back());
+        {
+            std::vector<int64_t> fill(toff.begin(), toff.end() - 1);
+            for (int l = 0; l < L; ++l)
+                for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
+                    int txs[2], tys[2], a, b;
+                    tiles_of(r, txs, tys, a, b);
+                    for (int yy = 0; yy < b; ++yy)
+                        for (int xx = 0; xx < a; ++xx)
+                            ent[fill[(size_t)l * nt + tys[yy] * g.ntx + txs[xx]]++] = (int)r;
+                }
+        }
+        // Regroup every list into groups of 4 entries whose windows do not overlap
+        // (circular distance >= 8 cells in x or y), padding with -1, so that the
+        // gridding kernel can add the 4 windows of a group at once without atomics.
+        // Greedy, in list order: an entry joins the first open group it fits; at
+        // most GROUP_OPEN groups are open, the oldest is closed (padded) to make room.
+        std::vector<int64_t> goff((size_t)L * nt + 1, 0);
+        std::vector<int> gent;
+        gent.reserve((size_t)(toff.back() + toff.back() / 4 + 64));
+        {
+            constexpr int GROUP_OPEN = 64;
+            struct Group {
+                int m;
+                int e[4], x[4], y[4];
+            };
+            auto circ = [](int d, int K) {
+                d &= K - 1;
+                return d < K - d ? d : K - d;
+            };
+            std::vector<Group> open;
+            auto emit = [&](const Group& g) {
+                for (int k = 0; k < 4; ++k) gent.push_back(k < g.m ? g.e[k] : -1);
+            };
+            for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
+                open.clear();
+                for (int64_t q = toff[tix]; q < toff[tix + 1]; ++q) {
+                    const int r = ent[q];
+                    const int64_t i = perm[r];
+                    const int x = (cellx[i] - 3) & (Kx - 1), y = (celly[i] - 3) & (Ky - 1);
+                    bool placed = false;
+                    for (size_t gi = 0; gi < open.size() && !placed; ++gi) {
+                        Group& g = open[gi];
+                        bool fits = true;
+                        for (int k = 0; k < g.m && fits; ++k)
+                            fits = circ(x - g.x[k], Kx) >= 8 || circ(y - g.y[k], Ky) >= 8;
+                        if (!fits) continue;
+                        g.e[g.m] = r;
+                        g.x[g.m] = x;
+                        g.y[g.m] = y;
+                        if (++g.m == 4) {
+                            emit(g);
+                            open.erase(open.begin() + gi);
+                        }
+                        placed = true;
                     }
-                    placed = true;
+                    if (placed) continue;
+                    if ((int)open.size() == GROUP_OPEN) {
+                        emit(open.front());
+                        open.erase(open.begin());
+                    }
+                    Group g{};
+                    g.m = 1;
+                    g.e[0] = r;
+                    g.x[0] = x;
+                    g.y[0] = y;
+                    open.push_back(g);
                 }
-                if (placed) continue;
-                if ((int)open.size() == GROUP_OPEN) {
-                    emit(open.front());
-                    open.erase(open.begin());
-                }
-                Group g{};
-                g.m = 1;
-                g.e[0] = r;
-                g.x[0] = x;
-                g.y[0] = y;
-                open.push_back(g);
-            }
-            for (const Group& g : open) emit(g);
-            goff[tix + 1] = (int64_t)gent.size();
-        }
-    }
-    p->n_ent = goff.back();
-    if (p->n_ent >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "too many gridding list entries");
-    HS_TRY(upload(p, (void**)&p->tile_off, goff));
-    HS_TRY(upload(p, (void**)&p->tile_ent, gent));
-    // work items: lists longer than GRID_CAP entries are split at group
-    // boundaries; split tiles are merged
-    {
-        std::vector<int> items, merges;
-        int slots = 0;
-        for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
-            const int64_t a = goff[tix], b = goff[tix + 1];
-            const int64_t ng = (b - a) / 4;
-            const int parts = ng * 4 <= GRID_CAP ? 1 : (int)((ng * 4 + GRID_CAP - 1) / GRID_CAP);
-            if (parts == 1) {
-                items.insert(items.end(), {(int)tix, (int)a, (int)b, -1});
-            } else {
-                merges.insert(merges.end(), {(int)tix, slots, parts});
-                for (int k = 0; k < parts; ++k) {
-                    const int64_t e0 = a + 4 * (ng * k / parts), e1 = a + 4 * (ng * (k + 1) / parts);
-                    items.insert(items.end(), {(int)tix, (int)e0, (int)e1, slots + k});
-                }
-                slots += parts;
+                for (const Group& g : open) emit(g);
+                goff[tix + 1] = (int64_t)gent.size();
             }
         }
-        p->n_items = (int64_t)items.size() / 4;
-        p->n_merges = (int64_t)merges.size() / 3;
-        HS_TRY(upload(p, &p->grid_items, items));
-        HS_TRY(upload(p, &p->grid_merges, merges));
-        HS_TRY(plan_alloc(p, &p->grid_partial, (size_t)std::max(slots, 1) * g.tx * g.ty * p->csize()));
+        p->n_ent = goff.back();
+        if (p->n_ent >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "too many gridding list entries");
+        HS_TRY(upload(p, (void**)&p->tile_off, goff));
+        HS_TRY(upload(p, (void**)&p->tile_ent, gent));
+        // work items: lists longer than GRID_CAP entries are split at group
+        // boundaries; split tiles are merged
+        {
+            std::vector<int> items, merges;
+            int slots = 0;
+            for (int64_t tix = 0; tix < (int64_t)L * nt; ++tix) {
+                const int64_t a = goff[tix], b = goff[tix + 1];
+                const int64_t ng = (b - a) / 4;
+                const int parts = ng * 4 <= GRID_CAP ? 1 : (int)((ng * 4 + GRID_CAP - 1) / GRID_CAP);
+                if (parts == 1) {
+                    items.insert(items.end(), {(int)tix, (int)a, (int)b, -1});
+                } else {
+                    merges.insert(merges.end(), {(int)tix, slots, parts});
+                    for (int k = 0; k < parts; ++k) {
+                        const int64_t e0 = a + 4 * (ng * k / parts), e1 = a + 4 * (ng * (k + 1) / parts);
+                        items.insert(items.end(), {(int)tix, (int)e0, (int)e1, slots + k});
+                    }
+                    slots += parts;
+                }
+            }
+            p->n_items = (int64_t)items.size() / 4;
+            p->n_merges = (int64_t)merges.size() / 3;
+            HS_TRY(upload(p, &p->grid_items, items));
+            HS_TRY(upload(p, &p->grid_merges, merges));
+            HS_TRY(plan_alloc(p, &p->grid_partial, (size_t)std::max(slots, 1) * g.tx * g.ty * p->csize()));
+        }
     }
+    if (sweep && !(p->flags & HS_PLAN_COMPENSATED)) p->n_ent = p->n_sw_ent;
     HS_TRY(upload(p, (void**)&p->off_d, p->off_h));
 
     // tables
