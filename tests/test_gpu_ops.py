@@ -18,6 +18,9 @@ CASES = {
     "ragged64": dict(n=64, L=4, M=(2000, 1503, 0, 911), seed=11),
     "rect": dict(nx=64, ny=32, L=3, M=(700, 333, 1200), seed=12),
     "wide_uv": dict(n=32, L=2, M=(900, 1000), seed=13, uv_std=1.4),
+    # coverage packed around u = v = 0: strips with thousands of windows in a few rows
+    # (gridding work items cut short), windows wrapping around both grid edges
+    "dense": dict(n=64, L=2, M=(6000, 3000), seed=17, uv_std=0.15),
     # large grids: every compile-time FFT size (K = 1024 rows and columns; K = 2048 and 4096
     # along either axis)
     "big512": dict(n=512, L=2, M=(500, 300), seed=14),
@@ -93,8 +96,9 @@ def test_compensated_gridding_matches_and_is_not_worse():
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_gpu_deterministic(prec):
-    """Both gridding kernels sum per-warp private tiles in a fixed order:
-    repeated adjoints are bitwise equal; the two kernels agree to rounding."""
+    """Both gridding kernels (the register sweep and the compensated tiles) add
+    in a fixed order: repeated adjoints are bitwise equal; the two kernels agree
+    to rounding."""
     c = _case("ragged64", prec)
     plan = make_plan(c, prec, compensated=True)
     a = host(plan.phi_adj(dev(c["Y"], prec, True)))
