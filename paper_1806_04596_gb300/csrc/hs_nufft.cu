@@ -134,7 +134,15 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __res
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    // two visibilities per group and step
+    // two visibilities per group and step; every lane keeps its partial of the
+    // group's 8 visibilities, and one reduce-scatter over the 8 lanes leaves
+    // visibility j's sum in lane j, so the epilogue runs once per group, one
+    // visibility per lane
+    static_assert(DEGRID_CHUNK == 8 * 32, "one visibility per lane of a group");
+    CT p8[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p8[k] = cx<R>(0, 0);
+#pragma unroll
     for (int it2 = 0; it2 < DEGRID_CHUNK / 32; it2 += 2) {
         if (beg + 32 * it2 >= end) break;   // uniform over the CTA
         int off[2];
@@ -171,18 +179,27 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __res
             acc[h].x *= pu[h];
             acc[h].y *= pu[h];
         }
+        p8[it2] = acc[0];
+        p8[it2 + 1] = acc[1];
+    }
+    // reduce-scatter: at distance o, lanes with bit o set keep the upper half
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1)
+    for (int o = 4; o >= 1; o >>= 1) {
+        const bool up = (j & o) != 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                acc[h].x += __shfl_xor_sync(0xffffffffu, acc[h].x, o);
-                acc[h].y += __shfl_xor_sync(0xffffffffu, acc[h].y, o);
-            }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t i = beg + grp + 32 * (it2 + h);
-            if (i >= end || j != 0) continue;
-            CT v = acc[h];
+        for (int k = 0; k < o; ++k) {
+            const CT send = up ? p8[k] : p8[k + o];
+            CT keep = up ? p8[k + o] : p8[k];
+            keep.x += __shfl_xor_sync(0xffffffffu, send.x, o);
+            keep.y += __shfl_xor_sync(0xffffffffu, send.y, o);
+            p8[k] = keep;
+        }
+    }
+    const CT mine = p8[0];
+    {
+        const int64_t i = beg + grp + 32 * j;
+        if (i < end) {
+            CT v = mine;
             if (a.w) v = cscale(v, a.w[i]);
             if (MODE == DOUT_CALLER) {
                 a.out[a.perm[i]] = v;
