@@ -31,10 +31,11 @@ constexpr int DIN = 2 * DQ + MAXF - 2;    // analysis input region side (46)
 constexpr int SIN = DIN + 4;              // its row stride (50: pair loads hit distinct banks)
 constexpr int SRO = 48;                   // row-filtered tile stride: lowpass at 0, highpass at 16
 constexpr int DC = DQ + MAXF / 2 - 1;     // synthesis coefficient region side (23)
-constexpr int SCF = 24;                   // its row stride
+constexpr int SCF = 24;                   // row stride of the column-filtered halves
+constexpr int SCS = 28;                   // row stride of the staged coefficients (16-byte chunks)
 constexpr int SCL = 2 * SCF + 1;          // column-filtered tile stride (x-lowpass at 0, highpass at 24)
 constexpr int FWD_SMEM = DIN * SIN + 2 * DIN * SRO;        // reals
-constexpr int INV_SMEM = 2 * 4 * DC * SCF + 2 * DQ * SCL;  // reals
+constexpr int INV_SMEM = 2 * 4 * DC * SCS + 2 * DQ * SCL;  // reals
 static_assert(2 * DQ * (DQ * 2 + 1) <= 2 * DQ * SCL, "output transpose fits the column tile");
 
 // Runs CALL(D) for the runtime wavelet index d (0..7) with D a compile-time
@@ -59,6 +60,14 @@ template <typename R> __device__ __forceinline__ void cp_async(R* dst, const R* 
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -75,13 +84,22 @@ __device__ __forceinline__ void st4(double* p, double a, double b, double c, dou
 
 // Stages rows [y0, y0 + ry) x columns [x0, x0 + rx) of a periodic block (indices
 // wrapped with the power-of-two masks) into in[r * SIN + c].
+// FP32 with an 8-byte aligned block (`pairs`): x0, rx and the block width are
+// even, so columns move as 8-byte pairs that never straddle the periodic wrap.
 template <typename R>
 __device__ __forceinline__ void stage_region(R* in, const R* __restrict__ base, int64_t stride, int ymask,
-                                             int xmask, int y0, int x0, int ry, int rx) {
+                                             int xmask, int y0, int x0, int ry, int rx, bool pairs) {
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    for (int r = wy; r < ry; r += 8) {
-        const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
-        for (int c = lane; c < rx; c += 32) cp_async(in + r * SIN + c, row + ((x0 + c) & xmask));
+    if (sizeof(R) == 4 && pairs) {
+        for (int r = wy; r < ry; r += 8) {
+            const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
+            for (int c = 2 * lane; c < rx; c += 64) cp_async8(in + r * SIN + c, row + ((x0 + c) & xmask));
+        }
+    } else {
+        for (int r = wy; r < ry; r += 8) {
+            const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
+            for (int c = lane; c < rx; c += 32) cp_async(in + r * SIN + c, row + ((x0 + c) & xmask));
+        }
     }
     cp_async_commit();
 }
@@ -190,7 +208,7 @@ template <typename R, int D> __device__ __forceinline__ void fwd_all(const FwdCt
 template <typename R>
 __global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* __restrict__ A,
                                                    R* __restrict__ ll_out, int L, int ny, int nx, int last,
-                                                   R sc) {
+                                                   R sc, int pairs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* in = reinterpret_cast<R*>(smem_raw);
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
@@ -201,7 +219,8 @@ __global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* 
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int k0y = ty * qy, k0x = tx * qx;
     const int64_t N = (int64_t)ny * nx;
-    stage_region(in, X + l * N, nx, ny - 1, nx - 1, 2 * k0y, 2 * k0x, 2 * qy + MAXF - 2, 2 * qx + MAXF - 2);
+    stage_region(in, X + l * N, nx, ny - 1, nx - 1, 2 * k0y, 2 * k0x, 2 * qy + MAXF - 2, 2 * qx + MAXF - 2,
+                 pairs != 0);
     cp_async_wait<0>();
     __syncthreads();
     R* A0 = A + l * N + (int64_t)(2 * k0y) * nx + 2 * k0x;
@@ -235,7 +254,7 @@ __global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ src
 #define HS_FWD(DD)                                                                                       \
     {                                                                                                    \
         constexpr int F = 2 * (DD + 1);                                                                  \
-        stage_region(in, base, mx, my - 1, mx - 1, 2 * k0y, 2 * k0x, 2 * qy + F - 2, 2 * qx + F - 2);    \
+        stage_region(in, base, mx, my - 1, mx - 1, 2 * k0y, 2 * k0x, 2 * qy + F - 2, 2 * qx + F - 2, true); \
         cp_async_wait<0>();                                                                              \
         __syncthreads();                                                                                 \
         fwd_rows<R, DD>(in, ro, 2 * qy + F - 2, qx);                                                     \
@@ -247,15 +266,41 @@ __global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ src
 }
 
 // ---- synthesis
+// Column offset of a staged coefficient tile: the staged columns start at the
+// 16-byte boundary at or below the tile's first column kx0 = t q - D, which is
+// kx0 - inv_co columns (q is a multiple of the chunk, or the tile is alone).
+template <typename R, int D> __host__ __device__ constexpr int inv_co() {
+    constexpr int EPC = 16 / (int)sizeof(R);
+    return (EPC - D % EPC) % EPC;
+}
+
 // Stages the four subband regions of one (d, l) tile: rows ky0 .. ky0 + cyn
-// and columns kx0 .. kx0 + cxn (periodic) into cf[s][row][col], s = 2 yb + xb;
-// subband 0 (LL) comes from `ll` (row stride lls).
-template <typename R>
+// and columns kx0 .. kx0 + cxn (periodic) into cf[s][row][CO + col], s = 2 yb + xb;
+// subband 0 (LL) comes from `ll` (row stride lls). With 16-byte aligned
+// coefficients (`chunks`), subbands at least one 16-byte chunk wide move in
+// aligned chunks (which never straddle the wrap).
+template <typename R, int CO>
 __device__ __forceinline__ void inv_stage(R* cf, const R* __restrict__ Ad, const R* __restrict__ ll,
                                           int64_t lls, int nx, int hy, int hx, int ky0, int kx0, int cyn,
-                                          int cxn) {
+                                          int cxn, bool chunks) {
+    constexpr int EPC = 16 / (int)sizeof(R);   // reals per chunk
+    constexpr int LPR = EPC == 4 ? 8 : 16;     // lanes per staged row (chunks per row <= LPR)
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    if (lane < cxn) {
+    if (chunks && hx >= EPC) {
+        const int nch = (cxn + CO + EPC - 1) / EPC;
+        const int cc = lane % LPR, rr = lane / LPR;
+        const int gx = (kx0 - CO + EPC * cc) & (hx - 1);
+        if (cc < nch) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                for (int yy = (32 / LPR) * wy + rr; yy < cyn; yy += 8 * (32 / LPR)) {
+                    const int gy = (ky0 + yy) & (hy - 1);
+                    const R* src = (s == 0) ? ll + (int64_t)gy * lls + gx
+                                            : Ad + (int64_t)((s >> 1) * hy + gy) * nx + (s & 1) * hx + gx;
+                    cp_async16(cf + (s * DC + yy) * SCS + EPC * cc, src);
+                }
+        }
+    } else if (lane < cxn) {
         const int gx = (kx0 + lane) & (hx - 1);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
@@ -263,7 +308,7 @@ __device__ __forceinline__ void inv_stage(R* cf, const R* __restrict__ Ad, const
                 const int gy = (ky0 + yy) & (hy - 1);
                 const R* src = (s == 0) ? ll + (int64_t)gy * lls + gx
                                         : Ad + (int64_t)((s >> 1) * hy + gy) * nx + (s & 1) * hx + gx;
-                cp_async(cf + (s * DC + yy) * SCF + lane, src);
+                cp_async(cf + (s * DC + yy) * SCS + CO + lane, src);
             }
     }
     cp_async_commit();
@@ -281,8 +326,8 @@ __device__ __forceinline__ void inv_cols(const R* __restrict__ cf, R* __restrict
     R a[NV], e[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
-        a[t] = cf[(b * DC + m0 + t) * SCF + x];
-        e[t] = cf[((2 + b) * DC + m0 + t) * SCF + x];
+        a[t] = cf[(b * DC + m0 + t) * SCS + inv_co<R, D>() + x];
+        e[t] = cf[((2 + b) * DC + m0 + t) * SCS + inv_co<R, D>() + x];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -360,10 +405,10 @@ __device__ __forceinline__ void tile_store(R* T, const R* acc, R* __restrict__ o
 template <typename R>
 __global__ void __launch_bounds__(256) k_dwt_inv_level(const R* __restrict__ A, const R* __restrict__ llbuf,
                                                       int ll_from_a, R* __restrict__ out, int L, int ny,
-                                                      int nx, int my, int mx) {
+                                                      int nx, int my, int mx, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* cf = reinterpret_cast<R*>(smem_raw);
-    R* cl = cf + 2 * 4 * DC * SCF;
+    R* cl = cf + 2 * 4 * DC * SCS;
     const int d = blockIdx.y / L, l = blockIdx.y - d * L;
     const int hy = my >> 1, hx = mx >> 1;
     const int qy = min(DQ, hy), qx = min(DQ, hx);
@@ -377,8 +422,8 @@ __global__ void __launch_bounds__(256) k_dwt_inv_level(const R* __restrict__ A, 
 #define HS_INV(DD)                                                                                   \
     {                                                                                                \
         constexpr int H = DD + 1;                                                                    \
-        inv_stage(cf, Ad, ll, lls, nx, hy, hx, ty * qy - (H - 1), tx * qx - (H - 1), qy + H - 1,     \
-                  qx + H - 1);                                                                       \
+        inv_stage<R, inv_co<R, DD>()>(cf, Ad, ll, lls, nx, hy, hx, ty * qy - (H - 1),                \
+                                      tx * qx - (H - 1), qy + H - 1, qx + H - 1, chunks != 0);       \
         cp_async_wait<0>();                                                                          \
         __syncthreads();                                                                             \
         inv_cols<R, DD>(cf, cl, qy, qx + H - 1);                                                     \
@@ -398,15 +443,16 @@ template <typename R> struct InvCtx {
     const R* A;
     const R* llbuf;
     int64_t N;
-    int L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a;
+    int L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a, chunks;
 };
 
 template <typename R, int D> __device__ __forceinline__ void inv_stage_d(const InvCtx<R>& c) {
     constexpr int H = D + 1;
     const R* Ad = c.A + ((int64_t)(1 + D) * c.L + c.l) * c.N;
     const R* ll = c.ll_from_a ? Ad : c.llbuf + ((int64_t)D * c.L + c.l) * (int64_t)c.hy * c.hx;
-    inv_stage(c.cf + (D & 1) * 4 * DC * SCF, Ad, ll, c.ll_from_a ? c.nx : c.hx, c.nx, c.hy, c.hx,
-              c.ty * c.qy - (H - 1), c.tx * c.qx - (H - 1), c.qy + H - 1, c.qx + H - 1);
+    inv_stage<R, inv_co<R, D>()>(c.cf + (D & 1) * 4 * DC * SCS, Ad, ll, c.ll_from_a ? c.nx : c.hx, c.nx, c.hy,
+                                 c.hx, c.ty * c.qy - (H - 1), c.tx * c.qx - (H - 1), c.qy + H - 1, c.qx + H - 1,
+                                 c.chunks != 0);
 }
 
 // Level-0 synthesis of all eight wavelets, the next wavelet's subbands staged
@@ -420,7 +466,7 @@ template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCt
             cp_async_wait<0>();
         }
         __syncthreads();
-        inv_cols<R, D>(c.cf + (D & 1) * 4 * DC * SCF, c.cl, c.qy, c.qx + D);
+        inv_cols<R, D>(c.cf + (D & 1) * 4 * DC * SCS, c.cl, c.qy, c.qx + D);
         __syncthreads();
         inv_rows<R, D>(c.cl, acc, c.qy, c.qx);
         inv_all<R, D + 1>(c, acc);
@@ -432,17 +478,17 @@ template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCt
 template <typename R>
 __global__ void __launch_bounds__(256) k_psi_adj_l0(const R* __restrict__ A, const R* __restrict__ llbuf,
                                                    int ll_from_a, R* __restrict__ X, int L, int ny, int nx,
-                                                   R s) {
+                                                   R s, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* cf = reinterpret_cast<R*>(smem_raw);
-    R* cl = cf + 2 * 4 * DC * SCF;
+    R* cl = cf + 2 * 4 * DC * SCS;
     const int l = blockIdx.y;
     const int hy = ny >> 1, hx = nx >> 1;
     const int qy = min(DQ, hy), qx = min(DQ, hx);
     const int ntx = hx / qx;
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int64_t N = (int64_t)ny * nx;
-    InvCtx<R> c{cf, cl, A, llbuf, N, L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a};
+    InvCtx<R> c{cf, cl, A, llbuf, N, L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a, chunks};
     inv_stage_d<R, 0>(c);
     R acc[4] = {0, 0, 0, 0};
     inv_all<R, 0>(c, acc);
@@ -501,8 +547,9 @@ template <typename R> static hs_status analysis_t(Plan* p, const R* X, R* A, cud
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
     const int top = p->levels - 1;
+    const int pairs = ((uintptr_t)X % 8) == 0;   // caller's image: 8-byte pairs only when aligned
     k_psi_fwd_l0<R><<<dim3(ntiles(ny, nx), L), 256, FWD_SMEM * sizeof(R), s>>>(X, A, buf[0], L, ny, nx, top == 0,
-                                                                              (R)(1.0 / 3.0));
+                                                                              (R)(1.0 / 3.0), pairs);
     HS_CHECK_LAUNCH();
     for (int lev = 1; lev <= top; ++lev) {
         const int my = ny >> lev, mx = nx >> lev;
@@ -515,6 +562,7 @@ template <typename R> static hs_status analysis_t(Plan* p, const R* X, R* A, cud
 }
 
 template <typename R> static hs_status synthesis_t(Plan* p, const R* A, R* X, cudaStream_t s) {
+    const int chunks = ((uintptr_t)A % 16) == 0;   // caller's coefficients: 16-byte chunks only when aligned
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
     const int top = p->levels - 1;
@@ -522,11 +570,12 @@ template <typename R> static hs_status synthesis_t(Plan* p, const R* A, R* X, cu
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
         k_dwt_inv_level<R><<<g, 256, INV_SMEM * sizeof(R), s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1],
-                                                                lev == top, buf[lev & 1], L, ny, nx, my, mx);
+                                                                lev == top, buf[lev & 1], L, ny, nx, my, mx,
+                                                                chunks);
         HS_CHECK_LAUNCH();
     }
     k_psi_adj_l0<R><<<dim3(ntiles(ny, nx), L), 256, INV_SMEM * sizeof(R), s>>>(
-        A, top == 0 ? nullptr : buf[1], top == 0, X, L, ny, nx, (R)(1.0 / 3.0));
+        A, top == 0 ? nullptr : buf[1], top == 0, X, L, ny, nx, (R)(1.0 / 3.0), chunks);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }

@@ -127,6 +127,25 @@ def test_psi_fwd_adj(prec, levels):
     assert rel(X, refX) <= TOL[prec], rel(X, refX)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_psi_unaligned_buffers(prec):
+    """Image and coefficient arrays starting one element past an aligned address
+    are staged element by element; the results equal those of aligned buffers."""
+    import torch
+    c = _case("rect", prec)
+    plan = make_plan(c, prec, levels=3)
+
+    def shifted(t):
+        s = torch.empty(t.numel() + 1, dtype=t.dtype, device=t.device)[1:].view_as(t)
+        s.copy_(t)
+        return s
+
+    X = dev(c["X"], prec)
+    A = plan.psi_fwd(X)
+    assert np.array_equal(host(plan.psi_fwd(shifted(X))), host(A))
+    assert np.array_equal(host(plan.psi_adj(shifted(A))), host(plan.psi_adj(A)))
+
+
 def test_psi_small_levels_long_filters():
     """64 x 64 at 4 levels: the coarsest level is 8 x 8, shorter than db8."""
     c = _case("ragged64", "f64")
