@@ -87,7 +87,7 @@ struct DgItem {
     int slot;     // partial-sum slot (PD mode)
 };
 constexpr int DG_REG = GRID_TILE + 8;   // staged region side (window start offsets 0..32)
-constexpr int DG_LDS = DG_REG + 1;
+constexpr int DG_LDS = DG_REG + 2;    // even: 16-byte aligned staged rows
 
 template <typename R> __device__ __forceinline__ void cp_async_cx(Cx<R>* dst, const Cx<R>* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -110,9 +110,20 @@ __global__ void __launch_bounds__(256) k_degrid(NufftK<R> a, const DgItem* __res
     const int Kx = a.g.Kx, Ky = a.g.Ky;
     const int ty0 = (t / a.g.ntx) * a.g.ty, tx0 = (t % a.g.ntx) * a.g.tx;
     const CT* G = a.grid + (int64_t)l * Ky * Kx;
-    for (int k = threadIdx.x; k < DG_REG * DG_REG; k += blockDim.x) {
-        const int r = k / DG_REG, c = k - r * DG_REG;
-        cp_async_cx<R>(S + r * DG_LDS + c, G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1)));
+    if constexpr (sizeof(R) == 4) {
+        // FP32: 16-byte chunks of two cells (tx0 and Kx even: a chunk never straddles the wrap)
+        constexpr int CPR = DG_REG / 2;   // chunks per staged row
+        for (int k = threadIdx.x; k < DG_REG * CPR; k += blockDim.x) {
+            const int r = k / CPR, c = 2 * (k - r * CPR);
+            const unsigned d = (unsigned)__cvta_generic_to_shared(S + r * DG_LDS + c);
+            const CT* src = G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+        }
+    } else {
+        for (int k = threadIdx.x; k < DG_REG * DG_REG; k += blockDim.x) {
+            const int r = k / DG_REG, c = k - r * DG_REG;
+            cp_async_cx<R>(S + r * DG_LDS + c, G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1)));
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     const int lane = threadIdx.x & 31;
