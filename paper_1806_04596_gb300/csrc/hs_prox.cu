@@ -84,6 +84,55 @@ __global__ void __launch_bounds__(256) k_l21(const R* __restrict__ A, const R* _
     }
 }
 
+// FP32 form of k_l21 for two neighbouring pixels per thread (8-byte loads and
+// stores; N even, buffers 8-byte aligned): the same operations per row, in
+// the same order.
+template <int LMAX>
+__global__ void __launch_bounds__(128) k_l21_pairs(const float* __restrict__ A, const float* __restrict__ W,
+                                                   const float* __restrict__ w_rows, float thr, int dual,
+                                                   float* __restrict__ out, int L, int64_t N) {
+    const int64_t Nh = N >> 1;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NB * Nh) return;
+    const int b = (int)(t / Nh);
+    const int64_t pix = 2 * (t - (int64_t)b * Nh);
+    const int64_t base = (int64_t)b * L * N + pix;
+    float2 q[LMAX];
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l)
+        if (l < L) {
+            float2 v = *reinterpret_cast<const float2*>(A + base + (int64_t)l * N);
+            if (W) {
+                const float2 u = *reinterpret_cast<const float2*>(W + base + (int64_t)l * N);
+                v.x += u.x;
+                v.y += u.y;
+            }
+            q[l] = v;
+        }
+    float s0 = 0, s1 = 0;
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l)
+        if (l < L) {
+            s0 = fmaf(q[l].x, q[l].x, s0);
+            s1 = fmaf(q[l].y, q[l].y, s1);
+        }
+    const float n0 = sqrtf(s0), n1 = sqrtf(s1);
+    float2 wr = make_float2(1.f, 1.f);
+    if (w_rows) wr = *reinterpret_cast<const float2*>(w_rows + (int64_t)b * N + pix);
+    const float lam0 = thr * wr.x, lam1 = thr * wr.y;
+    float f0, f1;
+    if (dual) {
+        f0 = (n0 > lam0) ? lam0 / n0 : 1.f;
+        f1 = (n1 > lam1) ? lam1 / n1 : 1.f;
+    } else {
+        f0 = (n0 > lam0) ? (n0 - lam0) / n0 : 0.f;
+        f1 = (n1 > lam1) ? (n1 - lam1) / n1 : 0.f;
+    }
+#pragma unroll
+    for (int l = 0; l < LMAX; ++l)
+        if (l < L) *reinterpret_cast<float2*>(out + base + (int64_t)l * N) = make_float2(q[l].x * f0, q[l].y * f1);
+}
+
 template <typename R>
 __global__ void k_l21_norm(const R* __restrict__ A, const R* __restrict__ w_rows, int L, int64_t N,
                            double* __restrict__ part) {
@@ -113,7 +162,17 @@ hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows
 #define HS_L21(R, LM)                                                                                    \
     k_l21<R, LM><<<g, 256, 0, s>>>((const R*)A, (const R*)Wadd, (const R*)w_rows, (R)thr, dual, (R*)out, L, \
                                    N)
-    if (p->prec == HS_F32) {
+    auto al8 = [](const void* q) { return ((uintptr_t)q % 8) == 0; };
+    const bool pairs = (N % 2) == 0 && al8(A) && al8(Wadd) && al8(w_rows) && al8(out);
+    if (p->prec == HS_F32 && pairs && L <= 64) {
+        const unsigned g2 = nblk((int64_t)NB * (N / 2), 128);
+        if (L <= 16)
+            k_l21_pairs<16><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
+                                               (float)thr, dual, (float*)out, L, N);
+        else
+            k_l21_pairs<64><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
+                                               (float)thr, dual, (float*)out, L, N);
+    } else if (p->prec == HS_F32) {
         if (L <= 16) HS_L21(float, 16);
         else if (L <= 64) HS_L21(float, 64);
         else HS_L21(float, 0);
@@ -426,6 +485,7 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int L, do
 // the output is often a small remainder of a large z (the dual form keeps the
 // small singular values).
 constexpr int LR_BS = 128;   // pixels (threads) per CTA
+static_assert(LR_DOUBLES % 2 == 0 && LRF_XL % 4 == 0 && MAX_L_NUC % 4 == 0, "16-byte aligned FP32 factor rows");
 
 template <typename R, int LMAX>
 __global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X, const R* __restrict__ Xa,
@@ -450,16 +510,25 @@ __global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X
     }
     for (int c = 0; c < r; ++c) {
         R p = 0, p2 = 0;
+        if constexpr (SPLIT) {   // the factor rows as 16-byte broadcast loads, same FMA order
 #pragma unroll
-        for (int i = 0; i < LMAX; ++i)
-            if (i < L) {
-                if (SPLIT) {
-                    p = fma(z[i], (R)Ff[LRF_XH + c * MAX_L_NUC + i], p);
-                    p2 = fma(z[i], (R)Ff[LRF_XL + c * MAX_L_NUC + i], p2);
-                } else {
-                    p = fma(z[i], (R)F[LR_X + c * MAX_L_NUC + i], p);
+            for (int i = 0; i < LMAX; i += 4)
+                if (i < L) {
+                    const float4 h = *reinterpret_cast<const float4*>(Ff + LRF_XH + c * MAX_L_NUC + i);
+                    const float4 o = *reinterpret_cast<const float4*>(Ff + LRF_XL + c * MAX_L_NUC + i);
+                    const float hh[4] = {h.x, h.y, h.z, h.w}, oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (i + k < L) {
+                            p = fma(z[i + k], (R)hh[k], p);
+                            p2 = fma(z[i + k], (R)oo[k], p2);
+                        }
                 }
-            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < LMAX; ++i)
+                if (i < L) p = fma(z[i], (R)F[LR_X + c * MAX_L_NUC + i], p);
+        }
         qs[c * LR_BS + t] = (SPLIT ? (R)Ff[LRF_G + c] : (R)F[LR_G + c]) * (p + p2);
     }
     if (!base)
@@ -467,16 +536,25 @@ __global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X
         for (int i = 0; i < LMAX; ++i) z[i] = 0;
     for (int c = 0; c < r; ++c) {
         const R q = qs[c * LR_BS + t];
+        if constexpr (SPLIT) {
 #pragma unroll
-        for (int i = 0; i < LMAX; ++i)
-            if (i < L) {
-                if (SPLIT) {
-                    z[i] = fma(q, (R)Ff[LRF_XH + c * MAX_L_NUC + i], z[i]);
-                    z[i] = fma(q, (R)Ff[LRF_XL + c * MAX_L_NUC + i], z[i]);
-                } else {
-                    z[i] = fma(q, (R)F[LR_X + c * MAX_L_NUC + i], z[i]);
+            for (int i = 0; i < LMAX; i += 4)
+                if (i < L) {
+                    const float4 h = *reinterpret_cast<const float4*>(Ff + LRF_XH + c * MAX_L_NUC + i);
+                    const float4 o = *reinterpret_cast<const float4*>(Ff + LRF_XL + c * MAX_L_NUC + i);
+                    const float hh[4] = {h.x, h.y, h.z, h.w}, oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (i + k < L) {
+                            z[i + k] = fma(q, (R)hh[k], z[i + k]);
+                            z[i + k] = fma(q, (R)oo[k], z[i + k]);
+                        }
                 }
-            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < LMAX; ++i)
+                if (i < L) z[i] = fma(q, (R)F[LR_X + c * MAX_L_NUC + i], z[i]);
+        }
     }
 #pragma unroll
     for (int i = 0; i < LMAX; ++i)
