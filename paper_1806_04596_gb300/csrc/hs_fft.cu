@@ -188,7 +188,7 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgN
 // LGK_ > 0: K = 2^LGK_ lines of G = 2^LGG_ per CTA fixed at compile time (the
 // pass schedule and every index computation fold to constants); 0: generic.
 template <typename R, int DIR, int MODE, int LGK_, int LGG_>
-__global__ void __launch_bounds__(512, 2) k_fft(FftArgs<R> a) {
+__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 2) k_fft(FftArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<R>* sm = reinterpret_cast<Cx<R>*>(smem_raw);
     if constexpr (LGK_ > 0) {
