@@ -128,6 +128,25 @@ def test_psi_fwd_adj(prec, levels):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_psi_256(prec):
+    """256 x 256 at 3 levels: 64 level-0 tiles and 16 level-1 tiles per wavelet
+    and channel, the chunked staging on every level."""
+    rng = np.random.default_rng(21)
+    c = rounded(dict(X=rng.uniform(0.0, 1.0, (2, 256, 256)), uv=np.zeros((1, 2)), Y=np.zeros(1, complex)), prec)
+    from paper_1806_04596_gb300 import hypersara as hs
+    plan = hs.Plan(256, 256, np.array([0, 1, 1]), dev(np.zeros((1, 2)), prec), levels=3, prec=prec)
+    A = host(plan.psi_fwd(dev(c["X"], prec)))
+    refA = wavelets.psi_adjoint_cube(c["X"], 3)
+    assert rel(A, refA) <= TOL[prec], rel(A, refA)
+    B = rng.standard_normal(refA.shape)
+    if prec == "f32":
+        B = B.astype(np.float32).astype(np.float64)
+    X = host(plan.psi_adj(dev(B, prec)))
+    refX = wavelets.psi_cube(B, 3)
+    assert rel(X, refX) <= TOL[prec], rel(X, refX)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_psi_unaligned_buffers(prec):
     """Image and coefficient arrays starting one element past an aligned address
     are staged element by element; the results equal those of aligned buffers."""
