@@ -20,5 +20,7 @@ from .cubes import (  # noqa: F401
     gaussian_blobs,
     power_law_spectra,
     uv_coverage,
+    uv_holes,
+    in_holes,
     noise_draws,
 )

@@ -9,7 +9,8 @@ for the sources (rank <= number of blobs, as the mixture model implies).
 
 Random streams: numpy Generator(PCG64(seed)), seed = 1000 * config + realisation.
 Draw order inside one problem is fixed: blobs, spectra, diffuse field (if
-any), uv pool, per-channel visibility counts (if uneven), noise.
+any), uv holes (if any), uv pool, per-channel visibility counts (if uneven),
+noise.
 """
 
 from __future__ import annotations
@@ -111,17 +112,48 @@ def diffuse_field(rng, nx: int, ny: int, slope: float = 1.5, peak: float = 0.1) 
     return peak * img / img.max()
 
 
-def uv_coverage(rng, M_max: int, freqs: np.ndarray, std: float, limit: float) -> np.ndarray:
+def uv_holes(rng, n_holes: int, std: float, limit: float, scale_max: float):
+    """Holes of the sampling function (Sec. 4.1: an inverse Gaussian profile, so
+    that the missing Fourier content sits mainly at high spatial frequencies).
+    Reading: n_holes discs at nu_0 whose centres are drawn inside the band with
+    density proportional to 1 - exp(-|c|^2 / (2 std^2)) (rejection sampling),
+    radii uniform in [0.04, 0.12] * limit / scale_max.
+
+    Returns (centres (n_holes, 2), radii (n_holes,))."""
+    edge = limit / scale_max
+    cs = np.empty((0, 2))
+    while cs.shape[0] < n_holes:
+        c = rng.uniform(-edge, edge, size=(4 * n_holes + 16, 2))
+        accept = rng.uniform(0.0, 1.0, size=c.shape[0]) < 1.0 - np.exp(-np.sum(c * c, axis=1) / (2 * std * std))
+        cs = np.concatenate([cs, c[accept]], axis=0)
+    cs = cs[:n_holes]
+    radii = rng.uniform(0.04, 0.12, size=n_holes) * edge
+    return cs, radii
+
+
+def in_holes(pts: np.ndarray, centres: np.ndarray, radii: np.ndarray) -> np.ndarray:
+    """True for the points (K, 2) inside any hole."""
+    if centres.shape[0] == 0:
+        return np.zeros(pts.shape[0], dtype=bool)
+    d2 = np.sum((pts[:, None, :] - centres[None, :, :]) ** 2, axis=2)
+    return np.any(d2 < radii[None, :] ** 2, axis=1)
+
+
+def uv_coverage(rng, M_max: int, freqs: np.ndarray, std: float, limit: float,
+                holes: int = 0) -> np.ndarray:
     """Base coverage at nu_0: i.i.d. N(0, std^2) per axis, rejecting points that
-    would leave the band [-limit, limit) once scaled to the highest channel.
+    would leave the band [-limit, limit) once scaled to the highest channel and,
+    with holes > 0, points inside the holes of uv_holes (drawn first).
 
     Returns the (M_max, 2) base pool at nu_0; channel l uses pool[:M_l] * nu_l / nu_0."""
     scale_max = freqs[-1] / freqs[0]
+    centres, radii = (uv_holes(rng, holes, std, limit, scale_max) if holes > 0
+                      else (np.zeros((0, 2)), np.zeros(0)))
     out = np.empty((0, 2))
     while out.shape[0] < M_max:
         need = M_max - out.shape[0]
         draw = rng.normal(0.0, std, size=(int(need * 1.3) + 16, 2))
-        keep = np.max(np.abs(draw), axis=1) * scale_max < limit
+        keep = (np.max(np.abs(draw), axis=1) * scale_max < limit) & ~in_holes(draw, centres, radii)
         out = np.concatenate([out, draw[keep]], axis=0)
     return out[:M_max]
 
@@ -136,7 +168,7 @@ def noise_draws(rng, n: int) -> np.ndarray:
 def make_inputs(config: int | dict, realisation: int = 0, *, n: int | None = None,
                 L: int | None = None, M=None, Q: int | None = None, seed: int | None = None,
                 insnr: float | None = None, f_lo: float | None = None,
-                f_hi: float | None = None) -> ProblemInputs:
+                f_hi: float | None = None, holes: int | None = None) -> ProblemInputs:
     """Draw one problem. Keyword arguments override the configuration's sizes
     (used for reduced parity cases of a configuration's generator)."""
     if isinstance(config, int):
@@ -159,6 +191,8 @@ def make_inputs(config: int | dict, realisation: int = 0, *, n: int | None = Non
         cfg["f_lo"] = f_lo
     if f_hi is not None:
         cfg["f_hi"] = f_hi
+    if holes is not None:
+        cfg["holes"] = holes
     if seed is None:
         seed = 1000 * cfg_id + realisation
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -181,7 +215,8 @@ def make_inputs(config: int | dict, realisation: int = 0, *, n: int | None = Non
         M_max = int(Mspec[1])
     else:
         M_max = int(Mspec)
-    pool = uv_coverage(rng, M_max, freqs, float(cfg["uv_std"]), float(cfg["uv_limit"]))
+    pool = uv_coverage(rng, M_max, freqs, float(cfg["uv_std"]), float(cfg["uv_limit"]),
+                       holes=int(cfg.get("holes", 0)))
     if isinstance(Mspec, (tuple, list)):
         Ml = rng.integers(int(Mspec[0]), int(Mspec[1]) + 1, size=Lc)
     else:

@@ -127,3 +127,14 @@ def test_pd_fp32_c2_shape_reduced_channels():
     Xg = host(st.get()[0])
     assert rel(Xg, ref.X) <= 1e-4
     assert abs(metrics.asnr(prob.truth, Xg) - metrics.asnr(prob.truth, ref.X)) <= 0.05
+
+
+def test_pd_fp64_holed_coverage():
+    """Configuration 1's generator with 20 holes in the uv coverage (Sec. 4.1),
+    FP64, 30 iterations."""
+    inp = synth.make_inputs(1, holes=20)
+    prob, prm = _setup(inp, "f64")
+    ref = pd.pd_solve(prob.op, prob.y, prob.eps, prm, 30)
+    _, st = _gpu_state(inp, prob, prm, "f64")
+    st.solve(30, graph=True)
+    assert rel(host(st.get()[0]), ref.X) <= 1e-11
