@@ -67,10 +67,11 @@ typedef enum {
 typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
 
 /* plan flags */
-/* Gridding adds one window per warp at a time with Kahan-compensated sums
- * (FP32 plans). Without it each warp adds 4 non-overlapping windows at once,
- * uncompensated: faster. Both keep per-warp private tiles summed in a fixed
- * order, so both are bitwise reproducible. */
+/* Gridding adds one window per warp at a time into per-warp tiles with
+ * Kahan-compensated sums (FP32 plans). Without it grids of at least 64 x 64
+ * cells use the register sweep (uncompensated, faster) and smaller grids add 4
+ * non-overlapping windows per warp pass into per-warp tiles. Every form sums in
+ * a fixed order, so all are bitwise reproducible. */
 #define HS_PLAN_COMPENSATED 1u
 
 typedef struct hs_plan* hs_plan_t;

@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
     }
 }
 
-// Default gridding kernel. The plan orders every tile list in groups of 4
+// Gridding kernel for grids smaller than 64 x 64 cells (the sweep needs
+// strips that no window reaches twice). The plan orders every tile list in groups of 4
 // entries whose windows do not overlap (padding -1). Each of the GRID_PW warps
 // of a CTA owns a private copy of the tile in shared memory and adds one group
 // per pass: 8 lanes per window (lane j: column j, all 8 rows; the row weights
