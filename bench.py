@@ -215,6 +215,18 @@ def _stage_traffic(stage: str, cfg_id: int):
 
 
 # ---------------------------------------------------------------- GPU arm
+def job_rate(ms: float, steps: int, world: int, device: str = "cuda"):
+    """Whole-job rate of `world` replicas that each ran `steps` steps: the
+    slowest rank's time (MAX all-reduce when world > 1) and steps * world / it."""
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, steps * world / (ms / 1e3)
+
+
 def run_ours(a):
     import torch
     import synth
@@ -270,11 +282,7 @@ def run_ours(a):
     barrier()
     ms = e0.elapsed_time(e1)
     clocks = clk.stop()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = a.steps * world / (ms / 1e3)
+    ms, value = job_rate(ms, a.steps, world)
     X, beta, rho = st.get()
     torch.cuda.synchronize()
     Xh = X.cpu().numpy().astype(np.float64)
