@@ -127,7 +127,14 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
             if (s1 != s0) strips[s1].push_back({k0y, ((k0x - s1 * GRID_TILE + 7) & (Kx - 1)) - 7, (int)r});
         }
         for (int st = 0; st < nstrip; ++st) {
-            const std::vector<Win>& ws = strips[st];
+            std::vector<Win>& ws = strips[st];
+            // by start row (then column, index): a row range is a contiguous run
+            std::sort(ws.begin(), ws.end(), [](const Win& a, const Win& b) {
+                return a.y != b.y ? a.y < b.y : (a.x != b.x ? a.x < b.x : a.r < b.r);
+            });
+            auto row_at = [&](int y) {   // first window starting in row >= y
+                return std::lower_bound(ws.begin(), ws.end(), y, [](const Win& w, int v) { return w.y < v; });
+            };
             std::fill(rowcnt.begin(), rowcnt.end(), 0);
             for (const Win& w : ws) ++rowcnt[w.y];
             for (int row0 = 0; row0 < Ky;) {
@@ -137,14 +144,19 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
                 while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= SWEEP_CAP))
                     cnt += rowcnt[row1++];
                 const int H = row1 - row0;
+                // windows starting in rows row0 - 7 .. row1 - 1 (circularly), in order of
+                // their start row relative to row0 (the wrapped rows come first)
                 seg.clear();
-                for (const Win& w : ws) {
-                    const int ry = ((w.y - row0 + 7) & (Ky - 1)) - 7;
-                    if (ry < H) seg.push_back({ry, w.x, w.r});
+                auto take = [&](int ya, int yb) {
+                    for (auto it = row_at(ya); it != ws.end() && it->y < yb; ++it)
+                        seg.push_back({((it->y - row0 + 7) & (Ky - 1)) - 7, it->x, it->r});
+                };
+                if (row0 >= 7) {
+                    take(row0 - 7, row1);
+                } else {
+                    take(Ky + row0 - 7, Ky);
+                    take(0, row1);
                 }
-                std::sort(seg.begin(), seg.end(), [](const Win& a, const Win& b) {
-                    return a.y != b.y ? a.y < b.y : (a.x != b.x ? a.x < b.x : a.r < b.r);
-                });
                 const int e0 = (int)ent.size();
                 open.clear();
                 size_t first = 0;
