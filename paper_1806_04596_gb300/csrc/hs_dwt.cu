@@ -403,9 +403,10 @@ __device__ __forceinline__ void tile_store(R* T, const R* acc, R* __restrict__ o
 // (compact, stride mx, into `out`) from its LL (`llbuf`: A[1+d] at the coarsest
 // level, else the coarser level's output, compact stride mx / 2) and A[1+d].
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_dwt_inv_level(const R* __restrict__ A, const R* __restrict__ llbuf,
-                                                      int ll_from_a, R* __restrict__ out, int L, int ny,
-                                                      int nx, int my, int mx, int chunks) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
+    k_dwt_inv_level(const R* __restrict__ A, const R* __restrict__ llbuf,
+                    int ll_from_a, R* __restrict__ out, int L, int ny,
+                    int nx, int my, int mx, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* cf = reinterpret_cast<R*>(smem_raw);
     R* cl = cf + 2 * 4 * DC * SCS;
@@ -476,9 +477,10 @@ template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCt
 // Level-0 synthesis summed over the 9 bases: X[l] = (A[0][l] + sum_d W_d^T A[1+d][l]) / 3,
 // one CTA per (output tile, channel).
 template <typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1) k_psi_adj_l0(const R* __restrict__ A, const R* __restrict__ llbuf,
-                                                   int ll_from_a, R* __restrict__ X, int L, int ny, int nx,
-                                                   R s, int chunks) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
+    k_psi_adj_l0(const R* __restrict__ A, const R* __restrict__ llbuf,
+                 int ll_from_a, R* __restrict__ X, int L, int ny, int nx,
+                 R s, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* cf = reinterpret_cast<R*>(smem_raw);
     R* cl = cf + 2 * 4 * DC * SCS;

@@ -98,7 +98,8 @@ template <typename R> __device__ __forceinline__ void cp_async_cx(Cx<R>* dst, co
 }
 
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) k_degrid(NufftK<R> a, const DgItem* __restrict__ items) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1)
+    k_degrid(NufftK<R> a, const DgItem* __restrict__ items) {
     typedef Cx<R> CT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CT* S = reinterpret_cast<CT*>(smem_raw);   // [DG_REG][DG_LDS]
@@ -551,8 +552,9 @@ __device__ __forceinline__ void sw_ld4(const double* p, double* v) {
 }
 
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1) k_grid_sweep(NufftK<R> a, const SweepItem* __restrict__ items,
-                                                             const int* __restrict__ ent, int n_items) {
+__global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1)
+    k_grid_sweep(NufftK<R> a, const SweepItem* __restrict__ items,
+                 const int* __restrict__ ent, int n_items) {
     typedef Cx<R> CT;
     __shared__ __align__(16) R stage[SW_WARPS][32 * SW_LD];
     __shared__ __align__(16) int sxs[SW_WARPS][32];   // start column of every slot (relative to the strip)
