@@ -409,6 +409,25 @@ HS_API hs_status hs_time_stage(hs_plan_t plan, int stage, const void* in, void* 
 HS_API hs_status hs_daubechies_lowpass(int p, double* out);
 HS_API hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err);
 
+/*
+ * hs_sweep_lists (host only): the gridding work lists a plan builds for the
+ * register-sweep kernel on grids of at least 64 x 64 cells (G_l^H of step 12,
+ * Sec. 2.1), for inspection. Input: L channels of windows given by their start
+ * cells k0x[r], k0y[r] (0 <= k0 < K: the cell of t = u K / (2 pi), minus 3,
+ * wrapped), channel-concatenated with offsets[L + 1] (offsets[0] = 0). Output:
+ * work items, 6 ints each (channel, 32-column strip, first output row, end
+ * row, entry range e0, e1), heaviest first; entries: window positions r in
+ * groups of 4 (-1 = padding) whose windows start in the same 8-row band of the
+ * item (relative rows -7 .. end - first - 1) and cover disjoint columns of the
+ * strip, groups in band order. Two-call form: with items or ent NULL only
+ * *n_items and *n_ent are written; otherwise they give the capacities (in
+ * items and entries) and receive the counts. Caller-owned host buffers.
+ * Errors: HS_ERR_ARG for non-power-of-two or small grids, bad offsets, start
+ * cells outside the grid, or short buffers.
+ */
+HS_API hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y,
+                                int* items, int64_t* n_items, int* ent, int64_t* n_ent);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,41 @@ hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err) {
     return HS_OK;
 }
 
+hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y,
+                         int* items, int64_t* n_items, int* ent, int64_t* n_ent) {
+    clear_error();
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (!pow2(Kx) || !pow2(Ky) || Kx < 2 * hs::GRID_TILE || Ky < 2 * hs::GRID_TILE)
+        return fail(HS_ERR_ARG, "hs_sweep_lists: Kx, Ky must be powers of two >= %d", 2 * hs::GRID_TILE);
+    if (L < 1 || offsets == nullptr || n_items == nullptr || n_ent == nullptr || offsets[0] != 0)
+        return fail(HS_ERR_ARG, "hs_sweep_lists: need L >= 1, offsets from 0 and the count pointers");
+    for (int l = 0; l < L; ++l)
+        if (offsets[l + 1] < offsets[l]) return fail(HS_ERR_ARG, "hs_sweep_lists: offsets must be nondecreasing");
+    const int64_t M = offsets[L];
+    if (M >= ((int64_t)1 << 31)) return fail(HS_ERR_ARG, "hs_sweep_lists: too many windows");
+    if (M > 0 && (k0x == nullptr || k0y == nullptr)) return fail(HS_ERR_ARG, "hs_sweep_lists: null start cells");
+    for (int64_t r = 0; r < M; ++r)
+        if (k0x[r] < 0 || k0x[r] >= Kx || k0y[r] < 0 || k0y[r] >= Ky)
+            return fail(HS_ERR_ARG, "hs_sweep_lists: start cell %lld outside the grid", (long long)r);
+    std::vector<hs::SweepItem> it;
+    std::vector<int> en;
+    HS_TRY(hs::sweep_lists(Kx, Ky, L, offsets, k0x, k0y, it, en));
+    if (items != nullptr && ent != nullptr) {
+        if (*n_items < (int64_t)it.size() || *n_ent < (int64_t)en.size())
+            return fail(HS_ERR_ARG, "hs_sweep_lists: buffers hold %lld items / %lld entries, need %lld / %lld",
+                        (long long)*n_items, (long long)*n_ent, (long long)it.size(), (long long)en.size());
+        for (size_t k = 0; k < it.size(); ++k) {
+            const hs::SweepItem& q = it[k];
+            const int v[6] = {q.l, q.strip, q.row0, q.row1, q.e0, q.e1};
+            for (int c = 0; c < 6; ++c) items[6 * k + c] = v[c];
+        }
+        std::copy(en.begin(), en.end(), ent);
+    }
+    *n_items = (int64_t)it.size();
+    *n_ent = (int64_t)en.size();
+    return HS_OK;
+}
+
 hs_status hs_plan_create(hs_plan_t* out, int nx, int ny, int L, const int64_t* vis_offsets,
                          const void* uv, const void* weights, const void* precond, int oversample,
                          int J, double kb_beta, int wavelet_levels, hs_prec prec, unsigned flags,

@@ -154,6 +154,10 @@ double kb_phihat(double f, int J, double beta);
 // Fits phi(m + f), f in [0,1), m = -J/2 .. J/2-1, as polynomials in s = 2f - 1
 // with `terms` coefficients each (ascending powers). Returns the max error / phi(0).
 double kb_poly_fit(int J, double beta, int terms, std::vector<double>* coef);
+// Sweep-gridding work lists (host only): windows with start cells k0x[r], k0y[r],
+// channel ranges off[0..L]; list entries are the positions r.
+hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0x, const int* k0y,
+                      std::vector<SweepItem>& items, std::vector<int>& ent);
 
 // ---------------------------------------------------------------- launches
 // Visibility input / output modes of the gridding and de-gridding kernels.

@@ -97,10 +97,10 @@ static hs_status download_real(const Plan* p, const void* src, int64_t n, std::v
 // stored by band. Rows are cut after SWEEP_HMAX rows, or earlier once the list
 // would pass SWEEP_CAP windows (at least one row per item). Items are stored
 // heaviest first.
-static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::vector<int>& cellx,
-                             const std::vector<int>& celly) {
-    const Geo& g = p->g;
-    const int Kx = g.Kx, Ky = g.Ky, L = g.L;
+// Host part: window start cells k0x[r], k0y[r] in the order the kernel indexes
+// them (list entries are these positions r), channel ranges off[0..L].
+hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs, const int* k0ys,
+                      std::vector<SweepItem>& items, std::vector<int>& ent) {
     const int nstrip = Kx / GRID_TILE;
     const int hmax = std::min(SWEEP_HMAX, Ky - 8);
     struct Win {
@@ -109,8 +109,8 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
     std::vector<std::vector<Win>> strips(nstrip);
     std::vector<int64_t> rowcnt(Ky);
     std::vector<Win> seg;
-    std::vector<SweepItem> items;
-    std::vector<int> ent;
+    items.clear();
+    ent.clear();
     struct Grp {
         int y, m;        // band, windows held
         uint32_t mask;   // strip columns covered
@@ -119,9 +119,8 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
     std::vector<Grp> open;
     for (int l = 0; l < L; ++l) {
         for (auto& v : strips) v.clear();
-        for (int64_t r = p->off_h[l]; r < p->off_h[l + 1]; ++r) {
-            const int64_t i = perm[r];
-            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+        for (int64_t r = off[l]; r < off[l + 1]; ++r) {
+            const int k0x = k0xs[r], k0y = k0ys[r];
             const int s0 = k0x / GRID_TILE, s1 = ((k0x + 7) & (Kx - 1)) / GRID_TILE;
             strips[s0].push_back({k0y, k0x - s0 * GRID_TILE, (int)r});
             if (s1 != s0) strips[s1].push_back({k0y, ((k0x - s1 * GRID_TILE + 7) & (Kx - 1)) - 7, (int)r});
@@ -188,6 +187,22 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
     std::stable_sort(items.begin(), items.end(), [](const SweepItem& a, const SweepItem& b) {
         return (a.e1 - a.e0) + 4 * (a.row1 - a.row0) > (b.e1 - b.e0) + 4 * (b.row1 - b.row0);
     });
+    return HS_OK;
+}
+
+static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::vector<int>& cellx,
+                             const std::vector<int>& celly) {
+    const int Kx = p->g.Kx, Ky = p->g.Ky;
+    const int64_t M = p->off_h[p->g.L];
+    std::vector<int> k0x(M), k0y(M);
+    for (int64_t r = 0; r < M; ++r) {
+        const int64_t i = perm[r];
+        k0x[r] = (cellx[i] - 3) & (Kx - 1);
+        k0y[r] = (celly[i] - 3) & (Ky - 1);
+    }
+    std::vector<SweepItem> items;
+    std::vector<int> ent;
+    HS_TRY(sweep_lists(Kx, Ky, p->g.L, p->off_h.data(), k0x.data(), k0y.data(), items, ent));
     p->n_sw_items = (int64_t)items.size();
     p->n_sw_ent = (int64_t)ent.size();
     HS_TRY(upload(p, &p->sw_items, items));

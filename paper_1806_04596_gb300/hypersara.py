@@ -90,6 +90,8 @@ _SIGS = {
     "hs_time_stage": ([_P, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_float), _P], C.c_int),
     "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "hs_sweep_lists": ([C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.POINTER(C.c_int64), _P,
+                        C.POINTER(C.c_int64)], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -137,6 +139,24 @@ def kb_poly_fit_error(beta: float, terms: int, J: int = 8) -> float:
     e = C.c_double()
     _check("hs_kb_poly_fit", load().hs_kb_poly_fit(J, beta, terms, C.byref(e)))
     return e.value
+
+
+def sweep_lists(Kx: int, Ky: int, offsets, k0x, k0y):
+    """hs_sweep_lists: the sweep-gridding work lists for windows with start
+    cells (k0x, k0y), channel ranges `offsets`. Returns (items (n, 6) int32:
+    channel, strip, row0, row1, e0, e1; entries int32, -1 = padding)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    kx = np.ascontiguousarray(k0x, dtype=np.int32)
+    ky = np.ascontiguousarray(k0y, dtype=np.int32)
+    L = len(off) - 1
+    ni, ne = C.c_int64(0), C.c_int64(0)
+    args = (Kx, Ky, L, off.ctypes.data, kx.ctypes.data, ky.ctypes.data)
+    _check("hs_sweep_lists", load().hs_sweep_lists(*args, None, C.byref(ni), None, C.byref(ne)))
+    items = np.zeros((max(ni.value, 1), 6), dtype=np.int32)
+    ent = np.zeros(max(ne.value, 1), dtype=np.int32)
+    _check("hs_sweep_lists", load().hs_sweep_lists(*args, items.ctypes.data, C.byref(ni), ent.ctypes.data,
+                                                   C.byref(ne)))
+    return items[:ni.value], ent[:ne.value]
 
 
 # ---------------------------------------------------------------- torch glue
