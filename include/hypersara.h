@@ -29,7 +29,7 @@
  *   Memory      pointers named "device" are CUDA device pointers the caller owns;
  *               the library never frees them and keeps no reference after the
  *               call returns, except where a create function says so. Plans and
- *               states own only what they derive (sorted coordinates, tile lists,
+ *               states own only what they derive (sorted coordinates, gridding lists,
  *               tables, scratch), allocated at creation: the compute entry points
  *               allocate nothing.
  *   Streams     `stream` is a cudaStream_t (NULL = legacy default stream). Compute
