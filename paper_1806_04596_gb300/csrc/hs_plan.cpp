@@ -142,7 +142,6 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
                 int row1 = row0;
                 while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= SWEEP_CAP))
                     cnt += rowcnt[row1++];
-                const int H = row1 - row0;
                 // windows starting in rows row0 - 7 .. row1 - 1 (circularly), in order of
                 // their start row relative to row0 (the wrapped rows come first)
                 seg.clear();
