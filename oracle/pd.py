@@ -34,9 +34,15 @@ t counts iterations from 1, vartheta starts at 0, beta^{(0)} is undefined (the
 first iteration never adjusts), and the new bounds serve from the next
 iteration (step 11 uses eps^{(t-1)}).
 
-Initial state: everything zero (the paper's "Given" does not fix it). Steps
-13-19 (adaptive bounds) are not applied: the simulations keep epsilon fixed.
-Data blocks: B = 1 per channel (M_l^b = I).
+Initial state: everything zero (the paper's "Given" does not fix it). By
+default the bounds stay fixed (as in the paper's simulations, Sec. 4.1) and
+there is one data block per channel (M_l^b = I); `adapt` and `blocks` above
+switch on steps 13-19 and several blocks per channel.
+
+Preconditioning (Sec. 3.3): with diagonal U the data-term updates are exactly
+the unpreconditioned ones applied to the operator U^{1/2} Phi, written in the
+variable v = U^{1/2} w of that problem's dual w; kappa_3 = 1 / ||U^{1/2} Phi||^2
+keeps the Condat-Vu condition of Sec. 3.4.
 """
 
 from __future__ import annotations
@@ -166,17 +172,20 @@ def pd_solve(op, y, eps, prm: PDParams, iters: int, U=None, state: PDState | Non
     return st
 
 
-def metric_norm2(dX, dP, dA, dv, op, prm: PDParams) -> float:
+def metric_norm2(dX, dP, dA, dv, op, prm: PDParams, U=None) -> float:
     """Squared norm of a state difference in the primal-dual metric
-        M = [[I / tau, -K^*], [-K, diag(1 / sigma_i)]],  K = [I; Psi^dagger; Phi],
+        M = [[I / tau, -K^*], [-K, diag(1 / sigma_i)]],  K = [I; Psi^dagger; U^{1/2} Phi],
     written for the scaled duals (y_i = kappa_i D_i, sigma_i = kappa_i):
         ||dX||^2 / tau - 2 sum_i kappa_i <K_i dX, dD_i> + sum_i kappa_i ||dD_i||^2.
-    The iteration is a proximal-point step in M (U = I), so the residual between
-    consecutive pairs (X^{t-1}, D^t) is nonincreasing."""
+    The data dual of the U^{1/2} Phi problem is w = U^{-1/2} v, so its terms are
+    ||U^{-1/2} dv||^2 - 2 Re<Phi dX, dv>. The iteration is a proximal-point step
+    in M, so the residual between consecutive pairs (X^{t-1}, D^t) is
+    nonincreasing."""
     s = np.sum(dX * dX) / prm.tau
     s += prm.kappa1 * (np.sum(dP * dP) - 2.0 * np.sum(dX * dP))
     KdX = wavelets.psi_adjoint_cube(dX, prm.levels)
     s += prm.kappa2 * (np.sum(dA * dA) - 2.0 * np.sum(KdX * dA))
     PhidX = op.forward(dX)
-    s += prm.kappa3 * (np.sum(np.abs(dv) ** 2) - 2.0 * np.sum(np.real(np.conj(PhidX) * dv)))
+    dv2 = np.abs(dv) ** 2 if U is None else np.abs(dv) ** 2 / np.asarray(U, dtype=np.float64)
+    s += prm.kappa3 * (np.sum(dv2) - 2.0 * np.sum(np.real(np.conj(PhidX) * dv)))
     return float(s)

@@ -77,9 +77,14 @@ def l21_norm(A: np.ndarray) -> float:
     return float(np.sum(prox.row_norms(A)))
 
 
+def mu_from_cube(X: np.ndarray, levels: int = 4) -> float:
+    """||X||_* / ||Psi^dagger X||_{2,1} of a cube (the ratio of Sec. 2.3)."""
+    return nuclear_norm(X) / l21_norm(wavelets.psi_adjoint_cube(X, levels))
+
+
 def estimate_mu(op, y, levels: int = 4) -> float:
-    Xd = dirty_cube(op, y)
-    return nuclear_norm(Xd) / l21_norm(wavelets.psi_adjoint_cube(Xd, levels))
+    """mu = ||X_dirty||_* / ||Psi^dagger X_dirty||_{2,1} (Sec. 2.3)."""
+    return mu_from_cube(dirty_cube(op, y), levels)
 
 
 def op_norm2(op: nufft.WidebandOperator, U=None, iters: int = 500, tol: float = 1e-10,

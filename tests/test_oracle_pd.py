@@ -126,7 +126,7 @@ def test_solve_approaches_data_fidelity_and_snr():
     assert np.all(st2.X >= 0)
 
 
-def test_mu_and_opnorm_sanity():
+def test_opnorm_matches_dense_operator():
     inp, prob = _small_problem()
     op = prob.op
     # power iteration against the dense operator's largest singular value
@@ -141,8 +141,59 @@ def test_mu_and_opnorm_sanity():
         Er = np.vstack([E.real, E.imag])
         best = max(best, np.linalg.norm(Er, 2) ** 2)
     assert problem.op_norm2(op) == pytest.approx(best, rel=1e-8)
+
+
+def _density_precond(op):
+    """U_m = 1 / (visibilities of the channel in the same cell of the
+    oversampled grid): uniform-weighting density, not constant."""
+    U = np.empty(int(op.offsets[-1]))
+    for l, ch in enumerate(op.ch):
+        cell = ch.iy[:, 3] * ch.Kx + ch.ix[:, 3]
+        _, inv, cnt = np.unique(cell, return_inverse=True, return_counts=True)
+        U[op.offsets[l]:op.offsets[l + 1]] = 1.0 / cnt[inv]
+    return U
+
+
+def test_constant_preconditioner_is_a_rescaled_problem():
+    """U = c I on (y, eps) is the unpreconditioned iteration on (y / sqrt(c),
+    eps / sqrt(c)): v = c u at every step, ||U^{1/2} Phi||^2 = c ||Phi||^2, and
+    the primal iterates coincide."""
+    inp, prob = _small_problem()
+    op = prob.op
+    c = 3.7
+    U = np.full(int(op.offsets[-1]), c)
+    n2 = problem.op_norm2(op)
+    assert problem.op_norm2(op, U) == pytest.approx(c * n2, rel=1e-8)
     mu = problem.estimate_mu(op, prob.y, levels=2)
-    Xd = problem.dirty_cube(op, prob.y)
-    ref = np.sum(np.linalg.svd(Xd.reshape(op.L, -1), compute_uv=False)) / np.sum(
-        prox.row_norms(wavelets.psi_adjoint_cube(Xd, 2)))
-    assert mu == pytest.approx(ref, rel=1e-12)
+    prm_u = pd.PDParams(mu=mu, tau=0.33, kappa3=1.0 / (c * n2), levels=2)
+    prm_1 = pd.PDParams(mu=mu, tau=0.33, kappa3=1.0 / n2, levels=2)
+    su = pd.pd_solve(op, prob.y, prob.eps, prm_u, 25, U=U)
+    s1 = pd.pd_solve(op, prob.y / np.sqrt(c), prob.eps / np.sqrt(c), prm_1, 25)
+    np.testing.assert_allclose(su.X, s1.X, rtol=1e-10, atol=1e-13 * np.abs(s1.X).max())
+    np.testing.assert_allclose(su.v, c * s1.v, rtol=1e-10, atol=1e-13 * np.abs(su.v).max())
+
+
+def test_preconditioned_fixed_point_residual_nonincreasing():
+    """Non-constant diagonal U (density weights): the iteration is the
+    unpreconditioned one on U^{1/2} Phi, so its residual in that problem's PD
+    metric is nonincreasing."""
+    inp, prob = _small_problem(M=300)
+    op = prob.op
+    U = _density_precond(op)
+    assert U.min() < 1.0 and U.max() == 1.0
+    mu = problem.estimate_mu(op, prob.y, levels=2)
+    k3 = 1.0 / problem.op_norm2(op, U)
+    prm = pd.PDParams(mu=mu, tau=0.33, kappa3=k3, levels=2)
+    hist = []
+    pd.pd_solve(op, prob.y, prob.eps, prm, 40, U=U,
+                callback=lambda s: hist.append((s.X.copy(), s.P.copy(), s.A.copy(), s.v.copy())))
+    Xs = [np.zeros_like(hist[0][0])] + [h[0] for h in hist]
+    res = []
+    for t in range(1, len(hist)):
+        res.append(pd.metric_norm2(Xs[t] - Xs[t - 1], hist[t][1] - hist[t - 1][1],
+                                   hist[t][2] - hist[t - 1][2], hist[t][3] - hist[t - 1][3],
+                                   op, prm, U=U))
+    res = np.array(res)
+    assert np.all(res >= -1e-12 * res[0])
+    assert np.all(res[1:] <= res[:-1] * (1 + 1e-9) + 1e-14 * res[0])
+    assert res[-1] < 0.5 * res[0]
