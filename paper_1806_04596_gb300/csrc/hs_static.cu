@@ -11,8 +11,14 @@
 //
 // Set-up: the first call on a device (with that device current) resolves the
 // array's device address with cudaGetSymbolAddress, which may load this
-// library's device code, and caches it per device; make that first call
-// before any stream capture that is meant to contain these launches.
+// library's device code, and caches it per device together with the unique
+// id of the CUDA context it belongs to; make that first call before any stream
+// capture that is meant to contain these launches. A call that finds a
+// different context current on the device (after cudaDeviceReset, or a
+// context destroyed and created again) resolves the address again, so a
+// cached address never outlives its context.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "hs_device.cuh"
@@ -28,6 +34,35 @@ static __device__ __align__(256) double g_ball_scratch[HS_L2BALL_STATIC_DOUBLES]
 
 static std::mutex g_scratch_mu;
 static double* g_scratch_ptr[STATIC_MAX_DEVICES] = {};
+static unsigned long long g_scratch_ctx[STATIC_MAX_DEVICES] = {};
+
+// Unique id of the calling thread's current CUDA context (0 when none is
+// current). The two driver functions are looked up through the runtime, so
+// the library has no link-time dependency on the driver library.
+static hs_status current_context_id(unsigned long long* id) {
+    using get_current_t = CUresult (*)(CUcontext*);
+    using get_id_t = CUresult (*)(CUcontext, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return fail(HS_ERR_CUDA, "hs_proj_l2ball_static: driver context queries unavailable");
+        get_current = reinterpret_cast<get_current_t>(f0);
+        get_id = reinterpret_cast<get_id_t>(f1);
+    }
+    CUcontext ctx = nullptr;
+    *id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS)
+        return fail(HS_ERR_CUDA, "hs_proj_l2ball_static: cuCtxGetCurrent failed");
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS)
+        return fail(HS_ERR_CUDA, "hs_proj_l2ball_static: cuCtxGetId failed");
+    return HS_OK;
+}
 
 static hs_status static_scratch(double** out) {
     int dev = -1;
@@ -36,12 +71,16 @@ static hs_status static_scratch(double** out) {
         return fail(HS_ERR_ARG, "hs_proj_l2ball_static: device %d beyond the supported %d", dev,
                     STATIC_MAX_DEVICES);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_ptr[dev] == nullptr) {
+    unsigned long long ctx = 0;
+    HS_TRY(current_context_id(&ctx));
+    if (g_scratch_ptr[dev] == nullptr || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* ptr = nullptr;
         const cudaError_t rc = cudaGetSymbolAddress(&ptr, g_ball_scratch);
         if (rc != cudaSuccess || ptr == nullptr)
             return fail(HS_ERR_CUDA, "hs_proj_l2ball_static: cudaGetSymbolAddress: %s", cudaGetErrorString(rc));
+        HS_TRY(current_context_id(&ctx));   // the lookup above makes the device's context current
         g_scratch_ptr[dev] = static_cast<double*>(ptr);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return HS_OK;
@@ -81,11 +120,13 @@ __global__ void __launch_bounds__(32) k_sball_scale(const double* __restrict__ p
     }
 }
 
+// Z and out may be the same buffer (in-place projection), so neither is
+// declared __restrict__; each thread reads z before writing the same index.
 template <typename R>
-__global__ void __launch_bounds__(256) k_sball_apply(const Cx<R>* __restrict__ Z, const Cx<R>* __restrict__ Y,
+__global__ void __launch_bounds__(256) k_sball_apply(const Cx<R>* Z, const Cx<R>* __restrict__ Y,
                                                     const int64_t* __restrict__ off, int L,
                                                     const double* __restrict__ scale, int dual,
-                                                    Cx<R>* __restrict__ out) {
+                                                    Cx<R>* out) {
     const int l = blockIdx.y;
     const int64_t end = off[l + 1];
     const R sc = (R)scale[l];

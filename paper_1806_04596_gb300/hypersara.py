@@ -180,6 +180,26 @@ def _ptr(t) -> Optional[int]:
     return C.c_void_p(t.data_ptr())
 
 
+def _args(*specs):
+    """Pointers of checked tensor arguments. Each spec is (tensor, name, dtype,
+    numel or None[, optional]): the C functions read and write `numel`
+    elements of `dtype` through the pointer and cannot check either, so every
+    mismatch is rejected here, for all arguments, before any pointer is taken
+    or anything is launched."""
+    for spec in specs:
+        t, name, dtype, numel = spec[:4]
+        optional = len(spec) > 4 and spec[4]
+        if t is None:
+            if optional:
+                continue
+            raise ValueError(f"{name} is required")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return [_ptr(spec[0]) for spec in specs]
+
+
 class Plan:
     """Measurement plan (hs_plan_create). uv: CUDA tensor (M, 2) of the plan's real dtype."""
 
@@ -240,6 +260,14 @@ class Plan:
         torch = _torch()
         return torch.empty(self.M, dtype=self.cdtype, device="cuda")
 
+    def _img(self, t, name: str, n_bases: int = 0):
+        """Argument spec of an image cube (or n_bases coefficient cubes) for _args."""
+        return (t, name, self.rdtype, self.L * self.ny * self.nx * (n_bases if n_bases else 1))
+
+    def _vis(self, t, name: str):
+        """Argument spec of a visibility vector for _args."""
+        return (t, name, self.cdtype, self.M)
+
     def close(self):
         if getattr(self, "h", None):
             load().hs_plan_destroy(self.h)
@@ -254,51 +282,61 @@ class Plan:
     # operators --------------------------------------------------------------
     def phi_fwd(self, X, Y=None):
         Y = self.vis() if Y is None else Y
-        _check("hs_phi_fwd", load().hs_phi_fwd(self.h, _ptr(X), _ptr(Y), _stream()))
+        pX, pY = _args(self._img(X, "X"), self._vis(Y, "Y"))
+        _check("hs_phi_fwd", load().hs_phi_fwd(self.h, pX, pY, _stream()))
         return Y
 
     def phi_adj(self, Y, X=None):
         X = self.cube() if X is None else X
-        _check("hs_phi_adj", load().hs_phi_adj(self.h, _ptr(Y), _ptr(X), _stream()))
+        pY, pX = _args(self._vis(Y, "Y"), self._img(X, "X"))
+        _check("hs_phi_adj", load().hs_phi_adj(self.h, pY, pX, _stream()))
         return X
 
     def psi_fwd(self, X, A=None):
         A = self.cube(9) if A is None else A
-        _check("hs_psi_fwd", load().hs_psi_fwd(self.h, _ptr(X), _ptr(A), _stream()))
+        pX, pA = _args(self._img(X, "X"), self._img(A, "A", 9))
+        _check("hs_psi_fwd", load().hs_psi_fwd(self.h, pX, pA, _stream()))
         return A
 
     def psi_adj(self, A, X=None):
         X = self.cube() if X is None else X
-        _check("hs_psi_adj", load().hs_psi_adj(self.h, _ptr(A), _ptr(X), _stream()))
+        pA, pX = _args(self._img(A, "A", 9), self._img(X, "X"))
+        _check("hs_psi_adj", load().hs_psi_adj(self.h, pA, pX, _stream()))
         return X
 
     def prox_l21(self, A, thr: float, w_rows=None, dual: bool = False, out=None):
         out = self.cube(9) if out is None else out
-        _check("hs_prox_l21", load().hs_prox_l21(self.h, _ptr(A), _ptr(w_rows), float(thr), int(dual),
-                                                 _ptr(out), _stream()))
+        nw = 9 * self.nx * self.ny
+        pA, pw, po = _args(self._img(A, "A", 9), (w_rows, "w_rows", self.rdtype, nw, True),
+                           self._img(out, "out", 9))
+        _check("hs_prox_l21", load().hs_prox_l21(self.h, pA, pw, float(thr), int(dual), po, _stream()))
         return out
 
     def prox_nuclear(self, X, thr: float, w_sv=None, dual: bool = False, out=None):
         """Returns (out, singular values as an FP64 CUDA tensor)."""
         torch = _torch()
         out = self.cube() if out is None else out
+        pX, pw, po = _args(self._img(X, "X"), (w_sv, "w_sv", torch.float64, self.L, True),
+                           self._img(out, "out"))
         sv = torch.empty(self.L, dtype=torch.float64, device="cuda")
-        _check("hs_prox_nuclear", load().hs_prox_nuclear(self.h, _ptr(X), _ptr(w_sv), float(thr),
-                                                         int(dual), _ptr(out), _ptr(sv), _stream()))
+        _check("hs_prox_nuclear", load().hs_prox_nuclear(self.h, pX, pw, float(thr), int(dual), po, _ptr(sv),
+                                                         _stream()))
         return out, sv
 
     def proj_l2ball(self, Z, Yd, eps, dual: bool = False, out=None):
         """eps: FP64 CUDA tensor (L,). Returns (out, rho) with rho = ||z_l - y_l||."""
         torch = _torch()
         out = self.vis() if out is None else out
+        pZ, pY, pe, po = _args(self._vis(Z, "Z"), self._vis(Yd, "Yd"), (eps, "eps", torch.float64, self.L),
+                               self._vis(out, "out"))
         rho = torch.empty(self.L, dtype=torch.float64, device="cuda")
-        _check("hs_proj_l2ball", load().hs_proj_l2ball(self.h, _ptr(Z), _ptr(Yd), _ptr(eps), int(dual),
-                                                       _ptr(out), _ptr(rho), _stream()))
+        _check("hs_proj_l2ball", load().hs_proj_l2ball(self.h, pZ, pY, pe, int(dual), po, _ptr(rho), _stream()))
         return out, rho
 
     def norm_l21(self, A, w_rows=None) -> float:
         r = C.c_double()
-        _check("hs_norm_l21", load().hs_norm_l21(self.h, _ptr(A), _ptr(w_rows), C.byref(r), _stream()))
+        pA, pw = _args(self._img(A, "A", 9), (w_rows, "w_rows", self.rdtype, 9 * self.nx * self.ny, True))
+        _check("hs_norm_l21", load().hs_norm_l21(self.h, pA, pw, C.byref(r), _stream()))
         return r.value
 
     def time_stage(self, stage: str, inp=None, out=None, reps: int = 20) -> float:
@@ -327,6 +365,10 @@ class PDState:
         coefficient: SARA; w_l21 is then 9 x L x ny x nx)."""
         if sparsity not in ("l21", "l1"):
             raise ValueError("sparsity must be 'l21' or 'l1'")
+        torch = _torch()
+        nw = 9 * plan.ny * plan.nx * (plan.L if sparsity == "l1" else 1)
+        pY, pe, _, _ = _args(plan._vis(Y, "Y"), (eps, "eps", torch.float64, plan.nblocks),
+                             (w_nuc, "w_nuc", torch.float64, plan.L, True), (w_l21, "w_l21", plan.rdtype, nw, True))
         self.plan = plan
         self.sparsity = sparsity
         self._refs = (w_nuc, w_l21)   # the state references these buffers
@@ -334,12 +376,14 @@ class PDState:
                        None if w_nuc is None else w_nuc.data_ptr(),
                        None if w_l21 is None else w_l21.data_ptr(), 1 if sparsity == "l1" else 0)
         h = C.c_void_p()
-        _check("hs_pd_state_create", load().hs_pd_state_create(plan.h, _ptr(Y), _ptr(eps), C.byref(prm),
+        _check("hs_pd_state_create", load().hs_pd_state_create(plan.h, pY, pe, C.byref(prm),
                                                                C.byref(h), _stream()))
         self.h = h
 
     def set_data(self, Y, eps):
-        _check("hs_pd_set_data", load().hs_pd_set_data(self.h, _ptr(Y), _ptr(eps), _stream()))
+        torch = _torch()
+        pY, pe = _args(self.plan._vis(Y, "Y"), (eps, "eps", torch.float64, self.plan.nblocks))
+        _check("hs_pd_set_data", load().hs_pd_set_data(self.h, pY, pe, _stream()))
 
     def step(self):
         _check("hs_pd_step", load().hs_pd_step(self.h, _stream()))
@@ -464,12 +508,18 @@ def proj_l2ball_static(offsets, Z, Yd, eps, dual=False, out=None, prec: str = "f
     torch = _torch()
     if prec not in ("f32", "f64"):
         raise ValueError("prec must be 'f32' or 'f64'")
+    cdt = torch.complex64 if prec == "f32" else torch.complex128
     L = int(offsets.numel()) - 1
     out = torch.empty_like(Z) if out is None else out
+    n = Z.numel()
+    args = _args((offsets, "offsets", torch.int64, None), (Z, "Z", cdt, None), (Yd, "Yd", cdt, n),
+                 (eps, "eps", torch.float64, max(L, 0)), (out, "out", cdt, n))
+    if L >= 1 and int(offsets[-1].item()) != n:   # the kernels index Z, Yd, out up to offsets[L]
+        raise ValueError(f"offsets[-1] = {int(offsets[-1].item())} differs from Z.numel() = {n}")
     rho = torch.empty(max(L, 0), dtype=torch.float64, device="cuda")
     _check("hs_proj_l2ball_static",
-           load().hs_proj_l2ball_static(L, _ptr(offsets), _ptr(Z), _ptr(Yd), _ptr(eps), HS_F32 if prec == "f32" else HS_F64, int(dual),
-                                        _ptr(out), _ptr(rho), _stream()))
+           load().hs_proj_l2ball_static(L, *args[:4], HS_F32 if prec == "f32" else HS_F64, int(dual), args[4],
+                                        _ptr(rho), _stream()))
     return out, rho
 
 
