@@ -73,6 +73,11 @@ typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
  * non-overlapping windows per warp pass into per-warp tiles. Every form sums in
  * a fixed order, so all are bitwise reproducible. */
 #define HS_PLAN_COMPENSATED 1u
+/* FP32 plans: form the nuclear prox's L x L Gram matrix with register-blocked
+ * FMA on the CUDA cores instead of the tensor cores (tcgen05, split TF32). The
+ * tensor-core form is the default; this one is kept as a comparison baseline
+ * and is used anyway when a buffer is not 16-byte aligned. */
+#define HS_PLAN_GRAM_FMA 2u
 
 typedef struct hs_plan* hs_plan_t;
 typedef struct hs_pd_state* hs_pd_state_t;
@@ -147,6 +152,18 @@ typedef struct {
 HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);
 
 /*
+ * hs_plan_check - synchronise the stream and report whether a kernel of this
+ * plan (or of a PD state on it) failed on the device since the last check
+ * (the flag is then cleared): HS_ERR_TIMEOUT if a bounded device-side wait
+ * expired, HS_ERR_ARG if an input was outside a kernel's range, HS_OK
+ * otherwise. The tensor-core Gram kernel of the nuclear prox (hs_gram) is the
+ * one that waits on the device (for its own tensor-core operations, 1 s
+ * bound) and the one with a range (|z| < 2^60); after such a failure its
+ * output is invalid. hs_pd_get performs the same check when it synchronises.
+ */
+HS_API hs_status hs_plan_check(hs_plan_t plan, void* stream);
+
+/*
  * hs_phi_fwd - Y = Phi(X): Y_l = Theta_l G_l F Z x_l for every channel
  * (Sec. 2.1, Eq. "inverse"). X: DEVICE L x ny x nx reals. Y: DEVICE total
  * complex values, caller order. F is the unnormalised DFT with a negative
@@ -203,6 +220,23 @@ HS_API hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, 
  */
 HS_API hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, double thr,
                           int dual, void* out, double* sv_out, void* stream);
+
+/*
+ * hs_gram - the L x L Gram matrix S = Z^T Z of the N x L matrix Z whose column
+ * l is channel l of X (+ Xadd when not NULL): the dense contraction inside
+ * the nuclear prox (Eq. "prox-L*", Algorithm 2 step 5). S_out: DEVICE L x L
+ * doubles, row-major (symmetric). Requires L <= 64.
+ * FP32 plans use the tensor cores (tcgen05, BF16 operands) on exact integer
+ * digits of z: per 64-pixel chunk and channel, z is quantised to 24 bits
+ * relative to the chunk's largest magnitude, split into three base-256 digits,
+ * and every digit product and tensor-core partial sum is an exact integer;
+ * chunk partials are combined with compensated FP32 sums and FP64 across
+ * CTAs, so |S - S_exact|_ij <~ 1e-7 sqrt(S_ii S_jj). Inputs need |z| < 2^60
+ * (else HS_ERR_ARG from hs_plan_check). The CUDA-core form (HS_PLAN_GRAM_FMA,
+ * and buffers not 16-byte aligned) sums runs of 32 pixels in FP32 with two-sum
+ * compensation. FP64 plans sum in FP64.
+ */
+HS_API hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, double* S_out, void* stream);
 
 /*
  * hs_proj_l2ball - per-channel projection onto B(y_l, eps_l) =
@@ -310,7 +344,8 @@ HS_API hs_status hs_pd_solve(hs_pd_state_t state, int iters, int graph, void* st
  * NULL) and the last iteration's diagnostics: *beta_host = ||X - X_prev|| / ||X||
  * (Algorithm 2 step 23) and rho_host[b] = ||U^{-1/2} vbar_b - y_b|| per data
  * block (HOST nblocks doubles, may be NULL). Synchronises the stream when beta_host or rho_host is
- * given.
+ * given, and then returns HS_ERR_TIMEOUT if a bounded device-side wait of the
+ * plan's kernels expired (see hs_plan_check).
  */
 HS_API hs_status hs_pd_get(hs_pd_state_t state, void* X, double* beta_host, double* rho_host,
                     void* stream);

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libhypersara.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["hs_tables.cpp", "hs_plan.cpp", "hs_fft.cu", "hs_nufft.cu", "hs_dwt.cu", "hs_prox.cu",
-           "hs_eig.cu", "hs_api.cu", "hs_static.cu"]
+           "hs_eig.cu", "hs_gram_tc.cu", "hs_api.cu", "hs_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + CSRC, "-I" + INCLUDE]

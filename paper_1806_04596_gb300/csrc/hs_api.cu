@@ -193,6 +193,24 @@ hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info) {
     return HS_OK;
 }
 
+// Read and clear the plan's device error flag (the stream is synchronised).
+static hs_status take_device_error(Plan* p, cudaStream_t s) {
+    int err = 0;
+    HS_CHECK_CUDA(cudaMemcpyAsync(&err, p->err_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (err == 0) return HS_OK;
+    HS_CHECK_CUDA(cudaMemsetAsync(p->err_d, 0, sizeof(int), s));
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (err & 1) return fail(HS_ERR_TIMEOUT, "a bounded device-side wait expired (tensor-core Gram)");
+    return fail(HS_ERR_ARG, "an input magnitude reached 2^60, beyond the tensor-core Gram's range");
+}
+
+hs_status hs_plan_check(hs_plan_t plan, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    return take_device_error(plan->p, S(stream));
+}
+
 hs_status hs_phi_fwd(hs_plan_t plan, const void* X, void* Y, void* stream) {
     clear_error();
     CHECK_PLAN(plan);
@@ -258,6 +276,19 @@ hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, dou
         return fail(HS_ERR_ARG, "hs_prox_nuclear: L = %d exceeds %d", plan->p->g.L, MAX_L_NUC);
     return nuclear_apply(plan->p, X, nullptr, w_sv, thr, dual, out, sv_out, nullptr, nullptr,
                          S(stream));
+}
+
+hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, double* S_out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (X == nullptr || S_out == nullptr) return fail(HS_ERR_ARG, "hs_gram: null buffer");
+    Plan* p = plan->p;
+    const int L = p->g.L;
+    if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "hs_gram: L = %d exceeds %d", L, MAX_L_NUC);
+    cudaStream_t s = S(stream);
+    HS_TRY(gram_matrix(p, X, Xadd, s));
+    HS_CHECK_CUDA(cudaMemcpyAsync(S_out, p->gram, (size_t)L * L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return HS_OK;
 }
 
 hs_status hs_proj_l2ball(hs_plan_t plan, const void* Z, const void* Yd, const double* eps, int dual,
@@ -706,7 +737,7 @@ hs_status hs_pd_get(hs_pd_state_t st, void* X, double* beta_host, double* rho_ho
     if (beta_host) HS_CHECK_CUDA(cudaMemcpyAsync(beta_host, st->beta, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (rho_host) HS_CHECK_CUDA(cudaMemcpyAsync(rho_host, st->rho, sizeof(double) * p->nblk,
                                                 cudaMemcpyDeviceToHost, s));
-    if (beta_host || rho_host) HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (beta_host || rho_host) return take_device_error(p, s);
     return HS_OK;
 }
 

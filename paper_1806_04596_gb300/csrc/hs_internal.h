@@ -133,6 +133,7 @@ struct Plan {
     double* eigf = nullptr;            // LR_TOTAL_DOUBLES: low-rank prox factor (layout above)
     double* sv = nullptr;              // MAX_L_NUC doubles
     double* dscal = nullptr;           // small per-channel doubles (4 * L)
+    int* err_d = nullptr;              // device error flag: a bounded device-side wait expired
     void* xbuf = nullptr;              // L * N reals (power iteration, misc)
     void* xbuf2 = nullptr;             // L * N reals
     int64_t device_bytes = 0;
@@ -222,6 +223,17 @@ hs_status l1_apply(Plan* p, const void* A, const void* Wadd, const void* w, doub
                    cudaStream_t s);
 hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
                         int dual, void* out, double* sv_out, float* warm, int* r_out, cudaStream_t s);
+// S = Z^T Z of Z = X (+ Xadd) into p->gram (L x L, row-major).
+hs_status gram_matrix(Plan* p, const void* X, const void* Xadd, cudaStream_t s);
+// Tensor-core Gram matrix of FP32 plans (hs_gram_tc.cu): set-up once per plan
+// creation, the conditions it needs (L <= 64, N a multiple of 64, 16-byte
+// aligned buffers), and the launch writing per-CTA upper-triangle partials
+// part[e * g + b], b < g = *ctas_out <= nparts; a bounded wait that expires
+// sets *err.
+hs_status gram_tc_init();
+bool gram_tc_usable(const void* X, const void* Xa, int L, int64_t N);
+hs_status gram_tc_launch(const float* X, const float* Xa, int L, int64_t N, double* part, int nparts, int* err,
+                         int* ctas_out, cudaStream_t s);
 // FP32 plans: mixed-precision eigendecomposition of the Gram matrix (hs_eig.cu).
 // warm: L x L FP32 eigenvectors of the previous call (updated in place) or null.
 hs_status eig_mixed_launch(const double* S, int L, const double* w_sv, double thr, int dual,

@@ -563,6 +563,9 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
     HS_TRY(plan_alloc(p, (void**)&p->eigf, sizeof(double) * LR_TOTAL_DOUBLES));
     HS_TRY(plan_alloc(p, (void**)&p->sv, sizeof(double) * MAX_L_NUC));
     HS_TRY(plan_alloc(p, (void**)&p->dscal, sizeof(double) * 6 * std::max(L, 1)));
+    HS_TRY(plan_alloc(p, (void**)&p->err_d, sizeof(int)));
+    HS_CHECK_CUDA(cudaMemsetAsync(p->err_d, 0, sizeof(int), s));
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
 }
 
@@ -582,7 +585,8 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
         nx % (1 << levels) || ny % (1 << levels))
         return fail(HS_ERR_ARG, "wavelet_levels %d incompatible with %d x %d", levels, nx, ny);
     if (prec != HS_F32 && prec != HS_F64) return fail(HS_ERR_ARG, "bad precision %d", (int)prec);
-    if (flags & ~(unsigned)HS_PLAN_COMPENSATED) return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
+    if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA))
+        return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
     HS_TRY(dwt_init());
     HS_TRY(fft_init());
     HS_TRY(nufft_init());

@@ -577,21 +577,34 @@ static hs_status lowrank_apply_t(Plan* p, const void* X, const void* Xa, void* o
     return HS_OK;
 }
 
+// Partial Gram matrices of Z = X (+ Xa) into p->part and their fixed-order sum
+// into p->gram (L x L, row-major): tensor cores (tcgen05,
+// exact BF16 digits) for FP32 plans whose buffers allow it, register-blocked
+// FMA otherwise (and for FP64 plans).
+hs_status gram_matrix(Plan* p, const void* X, const void* Xadd, cudaStream_t s) {
+    const int L = p->g.L;
+    const int64_t N = p->N();
+    const int P = L * (L + 1) / 2;
+    int nb = GRAM_CTAS;
+    if (p->prec == HS_F32 && !(p->flags & HS_PLAN_GRAM_FMA) && gram_tc_usable(X, Xadd, L, N)) {
+        HS_TRY(gram_tc_launch((const float*)X, (const float*)Xadd, L, N, p->part, GRAM_CTAS, p->err_d, &nb, s));
+    } else if (p->prec == HS_F32) {
+        k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, (const float*)Xadd, L, N, p->part);
+    } else {
+        k_gram<double><<<GRAM_CTAS, 256, 0, s>>>((const double*)X, (const double*)Xadd, L, N, p->part);
+    }
+    HS_CHECK_LAUNCH();
+    k_gram_reduce<<<P, 128, 0, s>>>(p->part, nb, L, p->gram);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
 hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* w_sv, double thr,
                         int dual, void* out, double* sv_out, float* warm, int* r_out,
                         cudaStream_t s) {
     const int L = p->g.L;
     if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "nuclear prox: L = %d exceeds %d", L, MAX_L_NUC);
-    const int64_t N = p->N();
-    const int P = L * (L + 1) / 2;
-    double* gpart = p->part;   // P * GRAM_CTAS doubles
-    if (p->prec == HS_F32)
-        k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, (const float*)Xadd, L, N, gpart);
-    else
-        k_gram<double><<<GRAM_CTAS, 256, 0, s>>>((const double*)X, (const double*)Xadd, L, N, gpart);
-    HS_CHECK_LAUNCH();
-    k_gram_reduce<<<P, 128, 0, s>>>(gpart, GRAM_CTAS, L, p->gram);
-    HS_CHECK_LAUNCH();
+    HS_TRY(gram_matrix(p, X, Xadd, s));
     if (p->prec == HS_F32) {
         // FP32 Jacobi (warm-started) + FP64 refinement of the active eigenpairs
         HS_TRY(eig_mixed_launch(p->gram, L, w_sv, thr, dual, p->eigf, sv_out, warm, r_out, s));
@@ -609,15 +622,7 @@ hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* 
 hs_status nuclear_svals(Plan* p, const void* X, double* sv_out, cudaStream_t s) {
     const int L = p->g.L;
     if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "singular values: L = %d exceeds %d", L, MAX_L_NUC);
-    const int64_t N = p->N();
-    const int P = L * (L + 1) / 2;
-    if (p->prec == HS_F32)
-        k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, nullptr, L, N, p->part);
-    else
-        k_gram<double><<<GRAM_CTAS, 256, 0, s>>>((const double*)X, nullptr, L, N, p->part);
-    HS_CHECK_LAUNCH();
-    k_gram_reduce<<<P, 128, 0, s>>>(p->part, GRAM_CTAS, L, p->gram);
-    HS_CHECK_LAUNCH();
+    HS_TRY(gram_matrix(p, X, nullptr, s));
     if (p->prec == HS_F32) return eig_mixed_launch(p->gram, L, nullptr, 0.0, 1, p->eigf, sv_out, nullptr, nullptr, s);
     return eig_f64_launch(p->gram, L, nullptr, 0.0, 1, p->eigf, sv_out, nullptr, s);
 }
@@ -682,7 +687,7 @@ hs_status reweight_sv(const double* sv, int L, double gamma, double* w_out, cuda
     return HS_OK;
 }
 
-hs_status prox_init() { return HS_OK; }
+hs_status prox_init() { return gram_tc_init(); }
 
 int64_t gram_part_doubles(int L) { return (int64_t)(L * (L + 1) / 2) * GRAM_CTAS; }
 

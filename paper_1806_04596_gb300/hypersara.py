@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libhypersara.so")
 HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_NOMEM, HS_ERR_TIMEOUT, HS_ERR_STATE = 0, -1, -2, -3, -4, -5
 HS_F32, HS_F64 = 0, 1
 HS_PLAN_COMPENSATED = 1
+HS_PLAN_GRAM_FMA = 2
 STAGES = {"fft_fwd": 0, "degrid": 1, "grid": 2, "fft_adj": 3, "psi_fwd": 4, "psi_adj": 5}
 
 _lib = None
@@ -67,12 +68,14 @@ _SIGS = {
     "hs_pd_bounds": ([_P, _P, _P, _P, _P], C.c_int),
     "hs_plan_destroy": ([_P], C.c_int),
     "hs_plan_info": ([_P, C.POINTER(PlanInfo)], C.c_int),
+    "hs_plan_check": ([_P, _P], C.c_int),
     "hs_phi_fwd": ([_P, _P, _P, _P], C.c_int),
     "hs_phi_adj": ([_P, _P, _P, _P], C.c_int),
     "hs_psi_fwd": ([_P, _P, _P, _P], C.c_int),
     "hs_psi_adj": ([_P, _P, _P, _P], C.c_int),
     "hs_prox_l21": ([_P, _P, _P, C.c_double, C.c_int, _P, _P], C.c_int),
     "hs_prox_nuclear": ([_P, _P, _P, C.c_double, C.c_int, _P, _P, _P], C.c_int),
+    "hs_gram": ([_P, _P, _P, _P, _P], C.c_int),
     "hs_proj_l2ball": ([_P, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hs_proj_l2ball_static": ([C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P], C.c_int),
     "hs_norm_l21": ([_P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
@@ -205,9 +208,10 @@ class Plan:
 
     def __init__(self, nx: int, ny: int, offsets: Sequence[int], uv, weights=None, precond=None,
                  oversample: int = 2, J: int = 8, kb_beta: float = 0.0, levels: int = 4,
-                 prec: str = "f32", compensated: bool = False, blocks=None):
+                 prec: str = "f32", compensated: bool = False, blocks=None, gram_fma: bool = False):
         """blocks: optional offsets (caller order) of intra-channel data blocks, containing
-        every channel boundary (hs_plan_create_blocks)."""
+        every channel boundary (hs_plan_create_blocks). gram_fma: form the nuclear prox's
+        Gram matrix on the CUDA cores instead of the tensor cores (HS_PLAN_GRAM_FMA)."""
         torch = _torch()
         lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -228,7 +232,7 @@ class Plan:
                                     off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                     _ptr(precond), oversample, J, float(kb_beta), levels,
                                     HS_F32 if prec == "f32" else HS_F64,
-                                    HS_PLAN_COMPENSATED if compensated else 0, _stream())
+                                    self._flags(compensated, gram_fma), _stream())
         else:
             bo = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64))
             self.blocks = bo
@@ -237,12 +241,20 @@ class Plan:
                                            bo.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                            _ptr(precond), oversample, J, float(kb_beta), levels,
                                            HS_F32 if prec == "f32" else HS_F64,
-                                           HS_PLAN_COMPENSATED if compensated else 0, _stream())
+                                           self._flags(compensated, gram_fma), _stream())
         _check("hs_plan_create", st)
         self.nblocks = len(self.blocks) - 1
         self.h = h
         self._keep = None
         self.M = int(off[-1])
+
+    @staticmethod
+    def _flags(compensated: bool, gram_fma: bool) -> int:
+        return (HS_PLAN_COMPENSATED if compensated else 0) | (HS_PLAN_GRAM_FMA if gram_fma else 0)
+
+    def check(self):
+        """hs_plan_check: synchronise and raise if a bounded device-side wait expired."""
+        _check("hs_plan_check", load().hs_plan_check(self.h, _stream()))
 
     # sizes ----------------------------------------------------------------
     @property
@@ -322,6 +334,14 @@ class Plan:
         _check("hs_prox_nuclear", load().hs_prox_nuclear(self.h, pX, pw, float(thr), int(dual), po, _ptr(sv),
                                                          _stream()))
         return out, sv
+
+    def gram(self, X, Xadd=None):
+        """hs_gram: the L x L Gram matrix of the cube X (+ Xadd), FP64 CUDA tensor."""
+        torch = _torch()
+        pX, pA = _args(self._img(X, "X"), self._img(Xadd, "Xadd") + (True,))
+        S = torch.empty((self.L, self.L), dtype=torch.float64, device="cuda")
+        _check("hs_gram", load().hs_gram(self.h, pX, pA, _ptr(S), _stream()))
+        return S
 
     def proj_l2ball(self, Z, Yd, eps, dual: bool = False, out=None):
         """eps: FP64 CUDA tensor (L,). Returns (out, rho) with rho = ||z_l - y_l||."""
