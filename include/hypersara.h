@@ -204,6 +204,15 @@ HS_API hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, 
                       int dual, void* out, void* stream);
 
 /*
+ * hs_l21_grad - gradient of the weighted l2,1 norm sum_n w_n ||a_n||_2 (Sec.
+ * 2.3): out_n = w_n a_n / ||a_n|| for every row n (across channels), 0 for a
+ * zero row (the minimum-norm subgradient there). A, w_rows and out as in
+ * hs_prox_l21; out may equal A. Used by the backward pass of the l2,1 term of
+ * differentiable objectives.
+ */
+HS_API hs_status hs_l21_grad(hs_plan_t plan, const void* A, const void* w_rows, void* out, void* stream);
+
+/*
  * hs_prox_nuclear - singular value soft threshold of the N x L matrix whose
  * column l is channel l (Eq. "prox-L*"), through the L x L Gram matrix
  * Z^T Z (FP64 accumulation) and its FP64 Jacobi eigendecomposition:

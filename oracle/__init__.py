@@ -18,6 +18,7 @@ Contents (each function cites the passage it follows):
   pd             preconditioned primal-dual iteration (Algorithm 2, fixed bounds)
   problem        data synthesis y = Phi(X) + noise, sigma, epsilon, mu, kappa_3
   metrics        SNR_l and aSNR (Sec. 4.3)
+  grad           gradient of 0.5 ||Phi X - y||^2 + ||Psi^dagger X||_{2,1}
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
 (closed forms, brute force, invariants). The whole PD solve has no external
@@ -25,4 +26,4 @@ implementation to compare against; it is pinned through its components and the
 monotone fixed-point residual of the iteration.
 """
 
-from . import kaiser_bessel, nufft, wavelets, prox, pd, problem, metrics  # noqa: F401
+from . import kaiser_bessel, nufft, wavelets, prox, pd, problem, metrics, grad  # noqa: F401

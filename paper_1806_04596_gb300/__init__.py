@@ -1,8 +1,10 @@
 """GB300 (sm_103a) implementation of the HyperSARA primal-dual hot path.
 
 The compute lives in libhypersara.so (CUDA kernels behind the C ABI declared
-in include/hypersara.h); `hypersara` is its ctypes binding and `problem`
-prepares a synthetic problem on the device with the library's own operators.
+in include/hypersara.h); `hypersara` is its ctypes binding, `autograd` exposes
+Phi and Psi as torch.autograd Functions (backward = the adjoint kernels) and a
+checkpointed unrolled PD solve, and `problem` prepares a synthetic problem on
+the device with the library's own operators.
 Importing this package does not load the library; the first call does, and
 raises if it has not been built.
 """

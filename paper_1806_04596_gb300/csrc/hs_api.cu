@@ -264,6 +264,13 @@ hs_status hs_prox_l21(hs_plan_t plan, const void* A, const void* w_rows, double 
     return l21_apply(plan->p, A, nullptr, w_rows, thr, dual, out, S(stream));
 }
 
+hs_status hs_l21_grad(hs_plan_t plan, const void* A, const void* w_rows, void* out, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    if (A == nullptr || out == nullptr) return fail(HS_ERR_ARG, "hs_l21_grad: null buffer");
+    return l21_apply(plan->p, A, nullptr, w_rows, 1.0, 2, out, S(stream));
+}
+
 hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, double thr, int dual,
                           void* out, double* sv_out, void* stream) {
     clear_error();

@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(256) k_l21(const R* __restrict__ A, const R* _
     const R nrm = sqrt(s);
     const R lam = thr * (w_rows ? w_rows[t] : (R)1);
     R f;
-    if (dual) f = (nrm > lam) ? lam / nrm : (R)1;
+    if (dual == 2) f = (nrm > (R)0) ? lam / nrm : (R)0;   // direction: gradient of lam ||q||
+    else if (dual) f = (nrm > lam) ? lam / nrm : (R)1;
     else f = (nrm > lam) ? (nrm - lam) / nrm : (R)0;
     if (LMAX > 0) {
 #pragma unroll
@@ -121,7 +122,10 @@ __global__ void __launch_bounds__(128) k_l21_pairs(const float* __restrict__ A, 
     if (w_rows) wr = *reinterpret_cast<const float2*>(w_rows + (int64_t)b * N + pix);
     const float lam0 = thr * wr.x, lam1 = thr * wr.y;
     float f0, f1;
-    if (dual) {
+    if (dual == 2) {   // direction: gradient of lam ||q||
+        f0 = (n0 > 0.f) ? lam0 / n0 : 0.f;
+        f1 = (n1 > 0.f) ? lam1 / n1 : 0.f;
+    } else if (dual) {
         f0 = (n0 > lam0) ? lam0 / n0 : 1.f;
         f1 = (n1 > lam1) ? lam1 / n1 : 1.f;
     } else {

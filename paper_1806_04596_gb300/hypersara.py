@@ -75,6 +75,7 @@ _SIGS = {
     "hs_psi_adj": ([_P, _P, _P, _P], C.c_int),
     "hs_prox_l21": ([_P, _P, _P, C.c_double, C.c_int, _P, _P], C.c_int),
     "hs_prox_nuclear": ([_P, _P, _P, C.c_double, C.c_int, _P, _P, _P], C.c_int),
+    "hs_l21_grad": ([_P, _P, _P, _P, _P], C.c_int),
     "hs_gram": ([_P, _P, _P, _P, _P], C.c_int),
     "hs_proj_l2ball": ([_P, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hs_proj_l2ball_static": ([C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P], C.c_int),
@@ -322,6 +323,15 @@ class Plan:
         pA, pw, po = _args(self._img(A, "A", 9), (w_rows, "w_rows", self.rdtype, nw, True),
                            self._img(out, "out", 9))
         _check("hs_prox_l21", load().hs_prox_l21(self.h, pA, pw, float(thr), int(dual), po, _stream()))
+        return out
+
+    def l21_grad(self, A, w_rows=None, out=None):
+        """hs_l21_grad: rows w_n a_n / ||a_n|| (0 for zero rows)."""
+        out = self.cube(9) if out is None else out
+        nw = 9 * self.nx * self.ny
+        pA, pw, po = _args(self._img(A, "A", 9), (w_rows, "w_rows", self.rdtype, nw, True),
+                           self._img(out, "out", 9))
+        _check("hs_l21_grad", load().hs_l21_grad(self.h, pA, pw, po, _stream()))
         return out
 
     def prox_nuclear(self, X, thr: float, w_sv=None, dual: bool = False, out=None):
