@@ -78,6 +78,13 @@ typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
  * tensor-core form is the default; this one is kept as a comparison baseline
  * and is used anyway when a buffer is not 16-byte aligned. */
 #define HS_PLAN_GRAM_FMA 2u
+/* Keep the default parameters instead of timing candidates at creation. By
+ * default a plan times, on itself, the sweep-gridding row cut and list cap
+ * ((32, 512), (64, 1024), (128, 2048)) and, for FP32 plans, the tensor-core
+ * against the CUDA-core Gram matrix, and keeps the fastest (choices cached per
+ * process by grid, L, visibilities, precision and flags; hs_plan_info reports
+ * them and the candidate times). */
+#define HS_PLAN_NO_TUNE 4u
 
 typedef struct hs_plan* hs_plan_t;
 typedef struct hs_pd_state* hs_pd_state_t;
@@ -147,6 +154,12 @@ typedef struct {
     double kb_fit_max_err;        /* max |poly - phi| / phi(0) of the kernel fit */
     int64_t device_bytes;         /* device memory held by the plan */
     int nblocks;                  /* data blocks (L unless created with hs_plan_create_blocks) */
+    int gram_tc;                  /* FP32 Gram matrix on the tensor cores (1) or CUDA cores (0) */
+    int sweep_hmax, sweep_cap;    /* sweep gridding: rows per work item, window cap per list */
+    int tuned;                    /* 0 defaults, 1 timed at creation, 2 from the process cache */
+    double tune_ms;               /* host time spent choosing */
+    double tune_grid_ms[3];       /* gridding launch per candidate (32, 64, 128 rows); 0 if not timed */
+    double tune_gram_ms[2];       /* Gram matrix: tensor cores, CUDA cores; 0 if not timed */
 } hs_plan_info_t;
 
 HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);
@@ -466,11 +479,14 @@ HS_API hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_e
  * strip, groups in band order. Two-call form: with items or ent NULL only
  * *n_items and *n_ent are written; otherwise they give the capacities (in
  * items and entries) and receive the counts. Caller-owned host buffers.
+ * Rows of an item are cut after hmax rows, or earlier once its list would pass
+ * cap windows (hmax, cap <= 0: the defaults 64 and 1024; the autotuner of
+ * hs_plan_create chooses among (32, 512), (64, 1024) and (128, 2048)).
  * Errors: HS_ERR_ARG for non-power-of-two or small grids, bad offsets, start
  * cells outside the grid, or short buffers.
  */
 HS_API hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y,
-                                int* items, int64_t* n_items, int* ent, int64_t* n_ent);
+                                int hmax, int cap, int* items, int64_t* n_items, int* ent, int64_t* n_ent);
 
 #ifdef __cplusplus
 }

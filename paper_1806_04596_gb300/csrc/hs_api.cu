@@ -90,8 +90,8 @@ hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err) {
     return HS_OK;
 }
 
-hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y,
-                         int* items, int64_t* n_items, int* ent, int64_t* n_ent) {
+hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y, int hmax,
+                         int cap, int* items, int64_t* n_items, int* ent, int64_t* n_ent) {
     clear_error();
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
     if (!pow2(Kx) || !pow2(Ky) || Kx < 2 * hs::GRID_TILE || Ky < 2 * hs::GRID_TILE)
@@ -108,7 +108,8 @@ hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const in
             return fail(HS_ERR_ARG, "hs_sweep_lists: start cell %lld outside the grid", (long long)r);
     std::vector<hs::SweepItem> it;
     std::vector<int> en;
-    HS_TRY(hs::sweep_lists(Kx, Ky, L, offsets, k0x, k0y, it, en));
+    HS_TRY(hs::sweep_lists(Kx, Ky, L, offsets, k0x, k0y, hmax > 0 ? hmax : hs::SWEEP_HMAX,
+                           cap > 0 ? cap : hs::SWEEP_CAP, it, en));
     if (items != nullptr && ent != nullptr) {
         if (*n_items < (int64_t)it.size() || *n_ent < (int64_t)en.size())
             return fail(HS_ERR_ARG, "hs_sweep_lists: buffers hold %lld items / %lld entries, need %lld / %lld",
@@ -190,6 +191,13 @@ hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info) {
     info->kb_fit_max_err = p->kb_fit_err;
     info->device_bytes = p->device_bytes;
     info->nblocks = p->nblk;
+    info->gram_tc = p->prec == HS_F32 ? p->gram_tc : 0;
+    info->sweep_hmax = p->sweep_hmax;
+    info->sweep_cap = p->sweep_cap;
+    info->tuned = p->tuned;
+    info->tune_ms = p->tune_ms;
+    for (int c = 0; c < 3; ++c) info->tune_grid_ms[c] = p->tune_grid_ms[c];
+    for (int c = 0; c < 2; ++c) info->tune_gram_ms[c] = p->tune_gram_ms[c];
     return HS_OK;
 }
 

@@ -134,10 +134,19 @@ struct Plan {
     double* sv = nullptr;              // MAX_L_NUC doubles
     double* dscal = nullptr;           // small per-channel doubles (4 * L)
     int* err_d = nullptr;              // device error flag: a bounded device-side wait expired
+    // parameters chosen by the plan-time autotuner (defaults without it)
+    int gram_tc = 1;                   // FP32 Gram matrix on the tensor cores (else CUDA cores)
+    int sweep_hmax = SWEEP_HMAX;       // sweep gridding: most output rows per work item
+    int sweep_cap = SWEEP_CAP;         // ... windows above which an item's rows are cut short
+    int tuned = 0;                     // 1: timed at creation, 2: taken from the process cache
+    double tune_ms = 0.0;              // host time spent tuning
+    double tune_grid_ms[3] = {0, 0, 0};   // gridding launch time per candidate
+    double tune_gram_ms[2] = {0, 0};      // Gram time: tensor cores, CUDA cores
     void* xbuf = nullptr;              // L * N reals (power iteration, misc)
     void* xbuf2 = nullptr;             // L * N reals
     int64_t device_bytes = 0;
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes;
 
     int64_t N() const { return (int64_t)g.nx * g.ny; }
     int64_t ntiles() const { return (int64_t)g.ntx * g.nty; }
@@ -157,8 +166,9 @@ double kb_phihat(double f, int J, double beta);
 double kb_poly_fit(int J, double beta, int terms, std::vector<double>* coef);
 // Sweep-gridding work lists (host only): windows with start cells k0x[r], k0y[r],
 // channel ranges off[0..L]; list entries are the positions r.
-hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0x, const int* k0y,
-                      std::vector<SweepItem>& items, std::vector<int>& ent);
+// Rows are cut after hmax rows, or earlier once a list would pass cap windows.
+hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0x, const int* k0y, int hmax,
+                      int cap, std::vector<SweepItem>& items, std::vector<int>& ent);
 
 // ---------------------------------------------------------------- launches
 // Visibility input / output modes of the gridding and de-gridding kernels.

@@ -16,8 +16,13 @@
 //  * the Kaiser-Bessel polynomial pieces, the Z scaling, the FFT twiddles;
 //  * all scratch buffers, so that no compute call allocates.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "hs_internal.h"
@@ -41,13 +46,27 @@ hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
         return fail(HS_ERR_NOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
     }
     p->allocs.push_back(*ptr);
+    p->alloc_bytes.push_back(bytes);
     p->device_bytes += (int64_t)bytes;
     return HS_OK;
+}
+
+// Free one allocation of the plan (lists rebuilt at creation).
+static void plan_release(Plan* p, void* ptr) {
+    for (size_t k = 0; k < p->allocs.size(); ++k)
+        if (p->allocs[k] == ptr) {
+            cudaFree(ptr);
+            p->device_bytes -= (int64_t)p->alloc_bytes[k];
+            p->allocs.erase(p->allocs.begin() + k);
+            p->alloc_bytes.erase(p->alloc_bytes.begin() + k);
+            return;
+        }
 }
 
 void plan_free(Plan* p) {
     for (void* q : p->allocs) cudaFree(q);
     p->allocs.clear();
+    p->alloc_bytes.clear();
 }
 
 static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -94,15 +113,15 @@ static hs_status download_real(const Plan* p, const void* src, int64_t n, std::v
 // column) and start in the same 8-row band (relative start row y, band
 // floor(y / 8)), so that they all lie in that band and the next. Windows are
 // placed in increasing start row, first fit over the band's groups; groups are
-// stored by band. Rows are cut after SWEEP_HMAX rows, or earlier once the list
-// would pass SWEEP_CAP windows (at least one row per item). Items are stored
+// stored by band. Rows are cut after hmax rows, or earlier once the list
+// would pass cap windows (at least one row per item). Items are stored
 // heaviest first.
 // Host part: window start cells k0x[r], k0y[r] in the order the kernel indexes
 // them (list entries are these positions r), channel ranges off[0..L].
-hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs, const int* k0ys,
-                      std::vector<SweepItem>& items, std::vector<int>& ent) {
+hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs, const int* k0ys, int hmax_req,
+                      int cap, std::vector<SweepItem>& items, std::vector<int>& ent) {
     const int nstrip = Kx / GRID_TILE;
-    const int hmax = std::min(SWEEP_HMAX, Ky - 8);
+    const int hmax = std::min(hmax_req, Ky - 8);
     struct Win {
         int y, x, r;   // start row (absolute, then relative to row0), start column relative to the strip
     };
@@ -140,7 +159,7 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
                 int64_t cnt = 0;
                 for (int d = 1; d <= 7; ++d) cnt += rowcnt[(row0 - d) & (Ky - 1)];
                 int row1 = row0;
-                while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= SWEEP_CAP))
+                while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= cap))
                     cnt += rowcnt[row1++];
                 // windows starting in rows row0 - 7 .. row1 - 1 (circularly), in order of
                 // their start row relative to row0 (the wrapped rows come first)
@@ -201,11 +220,131 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
     }
     std::vector<SweepItem> items;
     std::vector<int> ent;
-    HS_TRY(sweep_lists(Kx, Ky, p->g.L, p->off_h.data(), k0x.data(), k0y.data(), items, ent));
+    HS_TRY(sweep_lists(Kx, Ky, p->g.L, p->off_h.data(), k0x.data(), k0y.data(), p->sweep_hmax, p->sweep_cap, items,
+                       ent));
+    if (p->sw_items) {   // rebuilt by the autotuner: replace the previous lists
+        plan_release(p, p->sw_items);
+        plan_release(p, p->sw_ent);
+        p->sw_items = nullptr;
+        p->sw_ent = nullptr;
+    }
     p->n_sw_items = (int64_t)items.size();
     p->n_sw_ent = (int64_t)ent.size();
     HS_TRY(upload(p, &p->sw_items, items));
     HS_TRY(upload(p, (void**)&p->sw_ent, ent));
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Plan-time choice of the parameters that depend on the problem's size and
+// sampling density, by timing the candidates on this plan with CUDA events
+// (inputs: zeroed plan scratch; the values do not change the work):
+//   * sweep gridding row cut and list cap, (32, 512), (64, 1024), (128, 2048):
+//     short items balance dense coverage, tall items cut the halo rows;
+//   * FP32 Gram matrix of the nuclear prox on the tensor cores or the CUDA
+//     cores (the tensor-core form streams 64-pixel chunks per SM and wins on
+//     large cubes; the CUDA-core form wins when N L is small).
+// Choices are cached per process by (grid, L, visibilities, precision, flags),
+// so plans of the same shape skip the timing.
+namespace {
+struct TuneKey {
+    int Kx, Ky, L, prec;
+    unsigned flags;
+    int64_t M;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(Kx, Ky, L, prec, flags, M) < std::tie(o.Kx, o.Ky, o.L, o.prec, o.flags, o.M);
+    }
+};
+struct TuneVal {
+    int gram_tc, hmax, cap;
+    double grid_ms[3], gram_ms[2];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+}  // namespace
+
+static hs_status time_ms(cudaStream_t s, int reps, const std::function<hs_status()>& fn, double* out) {
+    HS_TRY(fn());   // warm-up
+    cudaEvent_t e0, e1;
+    HS_CHECK_CUDA(cudaEventCreate(&e0));
+    HS_CHECK_CUDA(cudaEventCreate(&e1));
+    hs_status st = HS_OK;
+    HS_CHECK_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && st == HS_OK; ++r) st = fn();
+    HS_CHECK_CUDA(cudaEventRecord(e1, s));
+    HS_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *out = ms / reps;
+    return st;
+}
+
+static hs_status autotune(Plan* p, const std::vector<int>& perm, const std::vector<int>& cellx,
+                          const std::vector<int>& celly, bool sweep, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const TuneKey key{p->g.Kx, p->g.Ky, p->g.L, (int)p->prec, p->flags, p->M_total};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const TuneVal& v = it->second;
+            p->gram_tc = v.gram_tc;
+            std::copy(v.grid_ms, v.grid_ms + 3, p->tune_grid_ms);
+            std::copy(v.gram_ms, v.gram_ms + 2, p->tune_gram_ms);
+            if (sweep && (v.hmax != p->sweep_hmax || v.cap != p->sweep_cap)) {
+                p->sweep_hmax = v.hmax;
+                p->sweep_cap = v.cap;
+                HS_TRY(build_sweep(p, perm, cellx, celly));
+            }
+            p->tuned = 2;
+            p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            return HS_OK;
+        }
+    }
+    const int L = p->g.L;
+    const int64_t N = p->N();
+    const int reps = 3;
+    if (sweep && !(p->flags & HS_PLAN_COMPENSATED) && p->M_total > 0) {
+        static const int cand[3][2] = {{32, 512}, {64, 1024}, {128, 2048}};
+        HS_CHECK_CUDA(cudaMemsetAsync(p->vis, 0, (size_t)p->M_total * p->csize(), s));
+        int best = -1;
+        for (int c = 0; c < 3; ++c) {
+            p->sweep_hmax = cand[c][0];
+            p->sweep_cap = cand[c][1];
+            HS_TRY(build_sweep(p, perm, cellx, celly));
+            GridArgs a{};
+            a.mode = GIN_SORTED;
+            a.in = p->vis;
+            HS_TRY(time_ms(s, reps, [&]() { return grid(p, a, s); }, &p->tune_grid_ms[c]));
+            if (best < 0 || p->tune_grid_ms[c] < p->tune_grid_ms[best]) best = c;
+        }
+        if (best != 2) {
+            p->sweep_hmax = cand[best][0];
+            p->sweep_cap = cand[best][1];
+            HS_TRY(build_sweep(p, perm, cellx, celly));
+        }
+    }
+    if (p->prec == HS_F32 && !(p->flags & HS_PLAN_GRAM_FMA) && L <= MAX_L_NUC) {
+        HS_CHECK_CUDA(cudaMemsetAsync(p->xbuf, 0, (size_t)L * N * p->rsize(), s));
+        HS_CHECK_CUDA(cudaMemsetAsync(p->xbuf2, 0, (size_t)L * N * p->rsize(), s));
+        for (int c = 0; c < 2; ++c) {
+            p->gram_tc = c == 0;
+            HS_TRY(time_ms(s, reps, [&]() { return gram_matrix(p, p->xbuf, p->xbuf2, s); }, &p->tune_gram_ms[c]));
+        }
+        p->gram_tc = p->tune_gram_ms[0] <= p->tune_gram_ms[1];
+    }
+    HS_CHECK_CUDA(cudaStreamSynchronize(s));
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        TuneVal v{p->gram_tc, p->sweep_hmax, p->sweep_cap, {}, {}};
+        std::copy(p->tune_grid_ms, p->tune_grid_ms + 3, v.grid_ms);
+        std::copy(p->tune_gram_ms, p->tune_gram_ms + 2, v.gram_ms);
+        g_tune_cache[key] = v;
+    }
+    p->tuned = 1;
+    p->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return HS_OK;
 }
 
@@ -565,6 +704,8 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
     HS_TRY(plan_alloc(p, (void**)&p->dscal, sizeof(double) * 6 * std::max(L, 1)));
     HS_TRY(plan_alloc(p, (void**)&p->err_d, sizeof(int)));
     HS_CHECK_CUDA(cudaMemsetAsync(p->err_d, 0, sizeof(int), s));
+    if (p->flags & HS_PLAN_GRAM_FMA) p->gram_tc = 0;
+    if (!(p->flags & HS_PLAN_NO_TUNE)) HS_TRY(autotune(p, perm, cellx, celly, sweep, s));
     HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
 }
@@ -585,7 +726,7 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
         nx % (1 << levels) || ny % (1 << levels))
         return fail(HS_ERR_ARG, "wavelet_levels %d incompatible with %d x %d", levels, nx, ny);
     if (prec != HS_F32 && prec != HS_F64) return fail(HS_ERR_ARG, "bad precision %d", (int)prec);
-    if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA))
+    if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA | HS_PLAN_NO_TUNE))
         return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
     HS_TRY(dwt_init());
     HS_TRY(fft_init());

@@ -590,7 +590,7 @@ hs_status gram_matrix(Plan* p, const void* X, const void* Xadd, cudaStream_t s) 
     const int64_t N = p->N();
     const int P = L * (L + 1) / 2;
     int nb = GRAM_CTAS;
-    if (p->prec == HS_F32 && !(p->flags & HS_PLAN_GRAM_FMA) && gram_tc_usable(X, Xadd, L, N)) {
+    if (p->prec == HS_F32 && p->gram_tc && gram_tc_usable(X, Xadd, L, N)) {
         HS_TRY(gram_tc_launch((const float*)X, (const float*)Xadd, L, N, p->part, GRAM_CTAS, p->err_d, &nb, s));
     } else if (p->prec == HS_F32) {
         k_gram<float><<<GRAM_CTAS, 256, 0, s>>>((const float*)X, (const float*)Xadd, L, N, p->part);

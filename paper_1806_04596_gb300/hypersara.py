@@ -23,6 +23,7 @@ HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_NOMEM, HS_ERR_TIMEOUT, HS_ERR_STATE = 0, 
 HS_F32, HS_F64 = 0, 1
 HS_PLAN_COMPENSATED = 1
 HS_PLAN_GRAM_FMA = 2
+HS_PLAN_NO_TUNE = 4
 STAGES = {"fft_fwd": 0, "degrid": 1, "grid": 2, "fft_adj": 3, "psi_fwd": 4, "psi_adj": 5}
 
 _lib = None
@@ -40,7 +41,9 @@ class PlanInfo(C.Structure):
                 ("total_vis", C.c_int64), ("grid_tile_entries", C.c_int64),
                 ("tile_x", C.c_int), ("tile_y", C.c_int), ("kb_terms", C.c_int),
                 ("kb_beta", C.c_double), ("kb_fit_max_err", C.c_double),
-                ("device_bytes", C.c_int64), ("nblocks", C.c_int)]
+                ("device_bytes", C.c_int64), ("nblocks", C.c_int),
+                ("gram_tc", C.c_int), ("sweep_hmax", C.c_int), ("sweep_cap", C.c_int), ("tuned", C.c_int),
+                ("tune_ms", C.c_double), ("tune_grid_ms", C.c_double * 3), ("tune_gram_ms", C.c_double * 2)]
 
 
 class AdaptParams(C.Structure):
@@ -94,7 +97,7 @@ _SIGS = {
     "hs_time_stage": ([_P, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_float), _P], C.c_int),
     "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
-    "hs_sweep_lists": ([C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, C.POINTER(C.c_int64), _P,
+    "hs_sweep_lists": ([C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int64), _P,
                         C.POINTER(C.c_int64)], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
@@ -145,16 +148,17 @@ def kb_poly_fit_error(beta: float, terms: int, J: int = 8) -> float:
     return e.value
 
 
-def sweep_lists(Kx: int, Ky: int, offsets, k0x, k0y):
+def sweep_lists(Kx: int, Ky: int, offsets, k0x, k0y, hmax: int = 0, cap: int = 0):
     """hs_sweep_lists: the sweep-gridding work lists for windows with start
-    cells (k0x, k0y), channel ranges `offsets`. Returns (items (n, 6) int32:
-    channel, strip, row0, row1, e0, e1; entries int32, -1 = padding)."""
+    cells (k0x, k0y), channel ranges `offsets`, rows cut after hmax rows or cap
+    windows (0: defaults). Returns (items (n, 6) int32: channel, strip, row0,
+    row1, e0, e1; entries int32, -1 = padding)."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     kx = np.ascontiguousarray(k0x, dtype=np.int32)
     ky = np.ascontiguousarray(k0y, dtype=np.int32)
     L = len(off) - 1
     ni, ne = C.c_int64(0), C.c_int64(0)
-    args = (Kx, Ky, L, off.ctypes.data, kx.ctypes.data, ky.ctypes.data)
+    args = (Kx, Ky, L, off.ctypes.data, kx.ctypes.data, ky.ctypes.data, int(hmax), int(cap))
     _check("hs_sweep_lists", load().hs_sweep_lists(*args, None, C.byref(ni), None, C.byref(ne)))
     items = np.zeros((max(ni.value, 1), 6), dtype=np.int32)
     ent = np.zeros(max(ne.value, 1), dtype=np.int32)
@@ -209,10 +213,12 @@ class Plan:
 
     def __init__(self, nx: int, ny: int, offsets: Sequence[int], uv, weights=None, precond=None,
                  oversample: int = 2, J: int = 8, kb_beta: float = 0.0, levels: int = 4,
-                 prec: str = "f32", compensated: bool = False, blocks=None, gram_fma: bool = False):
+                 prec: str = "f32", compensated: bool = False, blocks=None, gram_fma: bool = False,
+                 autotune: bool = True):
         """blocks: optional offsets (caller order) of intra-channel data blocks, containing
         every channel boundary (hs_plan_create_blocks). gram_fma: form the nuclear prox's
-        Gram matrix on the CUDA cores instead of the tensor cores (HS_PLAN_GRAM_FMA)."""
+        Gram matrix on the CUDA cores instead of the tensor cores (HS_PLAN_GRAM_FMA).
+        autotune=False keeps the default parameters (HS_PLAN_NO_TUNE)."""
         torch = _torch()
         lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -233,7 +239,7 @@ class Plan:
                                     off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                     _ptr(precond), oversample, J, float(kb_beta), levels,
                                     HS_F32 if prec == "f32" else HS_F64,
-                                    self._flags(compensated, gram_fma), _stream())
+                                    self._flags(compensated, gram_fma, autotune), _stream())
         else:
             bo = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64))
             self.blocks = bo
@@ -242,7 +248,7 @@ class Plan:
                                            bo.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                            _ptr(precond), oversample, J, float(kb_beta), levels,
                                            HS_F32 if prec == "f32" else HS_F64,
-                                           self._flags(compensated, gram_fma), _stream())
+                                           self._flags(compensated, gram_fma, autotune), _stream())
         _check("hs_plan_create", st)
         self.nblocks = len(self.blocks) - 1
         self.h = h
@@ -250,8 +256,9 @@ class Plan:
         self.M = int(off[-1])
 
     @staticmethod
-    def _flags(compensated: bool, gram_fma: bool) -> int:
-        return (HS_PLAN_COMPENSATED if compensated else 0) | (HS_PLAN_GRAM_FMA if gram_fma else 0)
+    def _flags(compensated: bool, gram_fma: bool, autotune: bool) -> int:
+        return ((HS_PLAN_COMPENSATED if compensated else 0) | (HS_PLAN_GRAM_FMA if gram_fma else 0)
+                | (0 if autotune else HS_PLAN_NO_TUNE))
 
     def check(self):
         """hs_plan_check: synchronise and raise if a bounded device-side wait expired."""
@@ -262,7 +269,11 @@ class Plan:
     def info(self) -> dict:
         inf = PlanInfo()
         _check("hs_plan_info", load().hs_plan_info(self.h, C.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+        out = {}
+        for k, _ in PlanInfo._fields_:
+            v = getattr(inf, k)
+            out[k] = list(v) if isinstance(v, C.Array) else v
+        return out
 
     def cube(self, n_bases: int = 0):
         torch = _torch()

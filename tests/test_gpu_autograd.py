@@ -71,7 +71,7 @@ def test_objective_gradient_vs_oracle_and_differences(cuda_device, prec):
     g = host(g)
     ref = ograd.gradient(op, X, y, 2)
     assert rel(g, ref) <= (1e-10 if prec == "f64" else 2e-5)
-    assert float(f) == pytest.approx(ograd.objective(op, X, y, 2), rel=1e-10 if prec == "f64" else 1e-5)
+    assert float(f.detach()) == pytest.approx(ograd.objective(op, X, y, 2), rel=1e-10 if prec == "f64" else 1e-5)
     # central differences with step 1e-3 along random directions
     for k in range(3):
         D = rng.standard_normal(X.shape)

@@ -32,12 +32,17 @@ def _rel_col(k0x, c0, Kx):
     return ((k0x - c0 + 7) % Kx) - 7
 
 
+# the autotuner's candidates (rows per item, window cap); (0, 0) = the defaults (64, 1024)
+CANDIDATES = [(0, 0), (32, 512), (128, 2048)]
+
+
+@pytest.mark.parametrize("hmax_req,cap", CANDIDATES)
 @pytest.mark.parametrize("Kx,Ky", [(64, 64), (128, 64), (64, 256)])
-def test_lists_meet_the_kernel_conditions(Kx, Ky):
+def test_lists_meet_the_kernel_conditions(Kx, Ky, hmax_req, cap):
     off, k0x, k0y, _ = _windows(3, Kx, Ky, 3, (1500, 0, 900))
-    items, ent = hs.sweep_lists(Kx, Ky, off, k0x, k0y)
+    items, ent = hs.sweep_lists(Kx, Ky, off, k0x, k0y, hmax_req, cap)
     L = len(off) - 1
-    hmax = min(64, Ky - 8)
+    hmax = min(hmax_req or 64, Ky - 8)
     rows = {}
     for (l, s, r0, r1, e0, e1) in items:
         assert 1 <= r1 - r0 <= hmax and (e1 - e0) % 4 == 0
@@ -70,7 +75,8 @@ def test_lists_meet_the_kernel_conditions(Kx, Ky):
     assert np.all(np.diff(work) <= 0)   # heaviest first
 
 
-def test_sweep_on_the_lists_equals_direct_gridding():
+@pytest.mark.parametrize("hmax_req,cap", CANDIDATES)
+def test_sweep_on_the_lists_equals_direct_gridding(hmax_req, cap):
     Kx, Ky = 128, 64
     off, k0x, k0y, rng = _windows(7, Kx, Ky, 2, (1200, 700))
     n = int(off[-1])
@@ -82,7 +88,7 @@ def test_sweep_on_the_lists_equals_direct_gridding():
             rows = (k0y[i] + np.arange(8)) % Ky
             cols = (k0x[i] + np.arange(8)) % Kx
             ref[l][np.ix_(rows, cols)] += val[i] * np.outer(phy[i], phx[i])
-    items, ent = hs.sweep_lists(Kx, Ky, off, k0x, k0y)
+    items, ent = hs.sweep_lists(Kx, Ky, off, k0x, k0y, hmax_req, cap)
     out = np.full((2, Ky, Kx), np.nan, complex)
     lanes = np.arange(T)
     for (l, s, r0, r1, e0, e1) in items:
