@@ -372,6 +372,26 @@ HS_API hs_status hs_pd_solve(hs_pd_state_t state, int iters, int graph, void* st
 HS_API hs_status hs_pd_get(hs_pd_state_t state, void* X, double* beta_host, double* rho_host,
                     void* stream);
 
+/*
+ * hs_pd_set_data_host - hs_pd_set_data from HOST buffers: y_l (HOST total
+ * complex of the plan's precision, caller order; pinned memory makes the copy
+ * asynchronous) and eps (HOST nblocks doubles) are copied to the device on the
+ * stream, then y is permuted into the state's order. The first call allocates
+ * a device staging buffer of the visibilities' size (kept by the state);
+ * later calls allocate nothing. The host buffers must stay valid until the
+ * stream reaches the copies.
+ */
+HS_API hs_status hs_pd_set_data_host(hs_pd_state_t state, const void* Y_host, const double* eps_host, void* stream);
+
+/*
+ * hs_pd_get_host - hs_pd_get into HOST memory: X_host (L x ny x nx reals of
+ * the plan's precision), *beta_host and rho_host (nblocks doubles) may be
+ * NULL except X_host. Synchronises the stream; returns HS_ERR_TIMEOUT or
+ * HS_ERR_ARG as hs_plan_check does when a kernel failed on the device.
+ */
+HS_API hs_status hs_pd_get_host(hs_pd_state_t state, void* X_host, double* beta_host, double* rho_host,
+                                void* stream);
+
 /* Number of kernel nodes in the state's captured iteration graph (0 before the
  * first hs_pd_solve with graph = 1): the kernel launches of one iteration. */
 HS_API hs_status hs_pd_graph_kernels(hs_pd_state_t state, int* out);

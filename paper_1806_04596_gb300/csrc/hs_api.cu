@@ -59,6 +59,7 @@ struct hs_pd_state {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    void* ystage = nullptr;   // caller-order y staged from host memory (hs_pd_set_data_host)
     std::vector<void*> allocs;
 };
 
@@ -618,6 +619,37 @@ hs_status hs_pd_set_data(hs_pd_state_t st, const void* Y, const double* eps, voi
         HS_CHECK_LAUNCH();
     }
     return HS_OK;
+}
+
+hs_status hs_pd_set_data_host(hs_pd_state_t st, const void* Y_host, const double* eps_host, void* stream) {
+    clear_error();
+    if (st == nullptr || eps_host == nullptr || (Y_host == nullptr && st->p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_pd_set_data_host: null argument");
+    Plan* p = st->p;
+    cudaStream_t s = S(stream);
+    const int64_t M = p->M_total;
+    if (M > 0 && st->ystage == nullptr) HS_TRY(st_alloc(st, &st->ystage, (size_t)M * p->csize()));
+    HS_CHECK_CUDA(cudaMemcpyAsync(st->eps, eps_host, p->nblk * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (M > 0) {
+        HS_CHECK_CUDA(cudaMemcpyAsync(st->ystage, Y_host, (size_t)M * p->csize(), cudaMemcpyHostToDevice, s));
+        const unsigned g = (unsigned)std::min<int64_t>((M + 255) / 256, 8192);
+        if (p->prec == HS_F32) k_gather_c2<<<g, 256, 0, s>>>((const float2*)st->ystage, p->perm, (float2*)st->y, M);
+        else k_gather_z2<<<g, 256, 0, s>>>((const double2*)st->ystage, p->perm, (double2*)st->y, M);
+        HS_CHECK_LAUNCH();
+    }
+    return HS_OK;
+}
+
+hs_status hs_pd_get_host(hs_pd_state_t st, void* X_host, double* beta_host, double* rho_host, void* stream) {
+    clear_error();
+    if (st == nullptr || X_host == nullptr) return fail(HS_ERR_ARG, "hs_pd_get_host: null argument");
+    cudaStream_t s = S(stream);
+    Plan* p = st->p;
+    HS_CHECK_CUDA(cudaMemcpyAsync(X_host, st->X, (size_t)p->g.L * p->N() * p->rsize(), cudaMemcpyDeviceToHost, s));
+    if (beta_host) HS_CHECK_CUDA(cudaMemcpyAsync(beta_host, st->beta, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (rho_host)
+        HS_CHECK_CUDA(cudaMemcpyAsync(rho_host, st->rho, sizeof(double) * p->nblk, cudaMemcpyDeviceToHost, s));
+    return take_device_error(p, s);
 }
 
 hs_status hs_pd_state_destroy(hs_pd_state_t st) {

@@ -87,6 +87,8 @@ _SIGS = {
     "hs_pd_state_create": ([_P, _P, _P, C.POINTER(PDParams), C.POINTER(C.c_void_p), _P], C.c_int),
     "hs_pd_state_destroy": ([_P], C.c_int),
     "hs_pd_set_data": ([_P, _P, _P, _P], C.c_int),
+    "hs_pd_set_data_host": ([_P, _P, _P, _P], C.c_int),
+    "hs_pd_get_host": ([_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "hs_pd_step": ([_P, _P], C.c_int),
     "hs_pd_solve": ([_P, C.c_int, C.c_int, _P], C.c_int),
     "hs_pd_get": ([_P, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
@@ -206,6 +208,28 @@ def _args(*specs):
         if numel is not None and t.numel() != numel:
             raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
     return [_ptr(spec[0]) for spec in specs]
+
+
+def _host_ptr(a, tdtype, numel: int, name: str, np_dtype=None):
+    """Pointer of a host buffer (torch CPU tensor or numpy array) after checking
+    its element type and count."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+        if tdtype is not None and a.dtype != tdtype:
+            raise ValueError(f"{name} must have dtype {tdtype}, got {a.dtype}")
+        if np_dtype is not None and a.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+        if a.numel() != numel:
+            raise ValueError(f"{name} must have {numel} elements, got {a.numel()}")
+        return C.c_void_p(a.data_ptr())
+    arr = np.asarray(a)
+    want = np_dtype if np_dtype is not None else {torch.complex64: np.complex64, torch.complex128: np.complex128,
+                                                    torch.float32: np.float32, torch.float64: np.float64}[tdtype]
+    if arr.dtype != want or not arr.flags["C_CONTIGUOUS"] or arr.size != numel:
+        raise ValueError(f"{name} must be a contiguous {np.dtype(want).name} array of {numel} elements")
+    return C.c_void_p(arr.ctypes.data)
 
 
 class Plan:
@@ -425,6 +449,23 @@ class PDState:
         torch = _torch()
         pY, pe = _args(self.plan._vis(Y, "Y"), (eps, "eps", torch.float64, self.plan.nblocks))
         _check("hs_pd_set_data", load().hs_pd_set_data(self.h, pY, pe, _stream()))
+
+    def set_data_host(self, Y, eps):
+        """hs_pd_set_data_host: Y is a host (preferably pinned) torch tensor or numpy
+        array of the plan's complex dtype, eps a host float64 array of one bound per
+        data block."""
+        yp = _host_ptr(Y, self.plan.cdtype, self.plan.M, "Y")
+        ep = _host_ptr(eps, None, self.plan.nblocks, "eps", np.float64)
+        _check("hs_pd_set_data_host", load().hs_pd_set_data_host(self.h, yp, ep, _stream()))
+
+    def get_host(self, X):
+        """hs_pd_get_host: copies X into the host tensor / array X (plan's real dtype);
+        returns (beta, rho per data block)."""
+        xp = _host_ptr(X, self.plan.rdtype, self.plan.L * self.plan.ny * self.plan.nx, "X")
+        beta = C.c_double()
+        rho = (C.c_double * self.plan.nblocks)()
+        _check("hs_pd_get_host", load().hs_pd_get_host(self.h, xp, C.byref(beta), rho, _stream()))
+        return beta.value, np.array(rho[:])
 
     def step(self):
         _check("hs_pd_step", load().hs_pd_step(self.h, _stream()))
