@@ -72,3 +72,17 @@ def make_plan(case, prec, levels=4, compensated=False, weights=None, precond=Non
 
 
 TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+def assert_close(out, ref, prec, elem=10.0):
+    """Relative 2-norm within the precision's tolerance, and every element
+    within elem * tolerance of the largest reference magnitude (so a few wrong
+    entries cannot hide under the norm)."""
+    out = np.asarray(out)
+    ref = np.asarray(ref)
+    r = rel(out, ref)
+    assert r <= TOL[prec], r
+    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+    if ref.size:
+        worst = float(np.max(np.abs(out - ref)))
+        assert worst <= elem * TOL[prec] * (scale if scale > 0 else 1.0), (worst, scale)

@@ -3,12 +3,14 @@
 Cases span several 32 x 32 gridding tiles (grid 128 x 128), uneven and empty
 channels, a rectangular image, weights, and wrap-around windows. Tolerances
 (relative 2-norm over the whole output): 1e-12 for FP64 plans, 1e-5 for FP32
-plans (inputs rounded to FP32 on both sides)."""
+plans (inputs rounded to FP32 on both sides), and every element within ten
+times that of the largest reference magnitude; channels without visibilities
+map to exact zeros."""
 
 import numpy as np
 import pytest
 
-from gpu_util import TOL, dev, host, make_plan, oracle_op, ragged_case, rel, rounded
+from gpu_util import TOL, assert_close, dev, host, make_plan, oracle_op, ragged_case, rel, rounded
 from oracle import nufft, prox, wavelets
 
 pytestmark = pytest.mark.gpu
@@ -47,8 +49,7 @@ def test_phi_fwd(prec, name):
     plan = make_plan(c, prec)
     Y = host(plan.phi_fwd(dev(c["X"], prec)))
     ref = oracle_op(c).forward(c["X"])
-    assert rel(Y, ref) <= TOL[prec], rel(Y, ref)
-    assert np.max(np.abs(Y - ref)) <= 10 * TOL[prec] * np.max(np.abs(ref))
+    assert_close(Y, ref, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -59,7 +60,10 @@ def test_phi_adj(prec, name, compensated):
     plan = make_plan(c, prec, compensated=compensated)
     X = host(plan.phi_adj(dev(c["Y"], prec, True)))
     ref = oracle_op(c).adjoint(c["Y"])
-    assert rel(X, ref) <= TOL[prec], rel(X, ref)
+    assert_close(X, ref, prec)
+    for l in range(c["L"]):   # a channel without visibilities maps to exactly zero
+        if c["off"][l + 1] == c["off"][l]:
+            assert not np.any(X[l])
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -70,8 +74,8 @@ def test_phi_with_weights(prec):
         w = w.astype(np.float32).astype(np.float64)
     plan = make_plan(c, prec, weights=w)
     op = nufft.WidebandOperator(c["nx"], c["ny"], c["uv"], c["off"], weights=w)
-    assert rel(host(plan.phi_fwd(dev(c["X"], prec))), op.forward(c["X"])) <= TOL[prec]
-    assert rel(host(plan.phi_adj(dev(c["Y"], prec, True))), op.adjoint(c["Y"])) <= TOL[prec]
+    assert_close(host(plan.phi_fwd(dev(c["X"], prec))), op.forward(c["X"]), prec)
+    assert_close(host(plan.phi_adj(dev(c["Y"], prec, True))), op.adjoint(c["Y"]), prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -118,13 +122,13 @@ def test_psi_fwd_adj(prec, levels):
     plan = make_plan(c, prec, levels=levels)
     A = host(plan.psi_fwd(dev(c["X"], prec)))
     refA = wavelets.psi_adjoint_cube(c["X"], levels)
-    assert rel(A, refA) <= TOL[prec], rel(A, refA)
+    assert_close(A, refA, prec)
     B = np.random.default_rng(2).standard_normal(refA.shape)
     if prec == "f32":
         B = B.astype(np.float32).astype(np.float64)
     X = host(plan.psi_adj(dev(B, prec)))
     refX = wavelets.psi_cube(B, levels)
-    assert rel(X, refX) <= TOL[prec], rel(X, refX)
+    assert_close(X, refX, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -137,13 +141,13 @@ def test_psi_256(prec):
     plan = hs.Plan(256, 256, np.array([0, 1, 1]), dev(np.zeros((1, 2)), prec), levels=3, prec=prec)
     A = host(plan.psi_fwd(dev(c["X"], prec)))
     refA = wavelets.psi_adjoint_cube(c["X"], 3)
-    assert rel(A, refA) <= TOL[prec], rel(A, refA)
+    assert_close(A, refA, prec)
     B = rng.standard_normal(refA.shape)
     if prec == "f32":
         B = B.astype(np.float32).astype(np.float64)
     X = host(plan.psi_adj(dev(B, prec)))
     refX = wavelets.psi_cube(B, 3)
-    assert rel(X, refX) <= TOL[prec], rel(X, refX)
+    assert_close(X, refX, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -190,10 +194,10 @@ def test_prox_l21(prec, dual):
     thr = 1.3
     out = host(plan.prox_l21(dev(A, prec), thr, dev(w, prec), dual=dual))
     ref = prox.l21_dual(A, w, thr) if dual else prox.prox_l21(A, w, thr)
-    assert rel(out, ref) <= TOL[prec]
+    assert_close(out, ref, prec)
     out1 = host(plan.prox_l21(dev(A, prec), thr, None, dual=dual))
     ref1 = prox.l21_dual(A, 1.0, thr) if dual else prox.prox_l21(A, 1.0, thr)
-    assert rel(out1, ref1) <= TOL[prec]
+    assert_close(out1, ref1, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -223,7 +227,9 @@ def test_prox_nuclear(prec, dual, L):
         ref, _ = prox.nuclear_dual(X, w, thr)
     else:
         ref = prox.prox_nuclear(X, w, thr)
-    assert rel(out, ref) <= (1e-11 if prec == "f64" else 1e-5), rel(out, ref)
+    tol = 1e-11 if prec == "f64" else 1e-5
+    assert rel(out, ref) <= tol, rel(out, ref)
+    assert np.max(np.abs(out - ref)) <= 10 * tol * np.max(np.abs(ref))
     svh = host(sv)
     if prec == "f64":
         assert rel(svh, ref_s) <= 1e-12
@@ -257,7 +263,7 @@ def test_proj_l2ball(prec, dual):
         a, b = c["off"][l], c["off"][l + 1]
         ref[a:b] = prox.l2ball_dual(Z[a:b], Yd[a:b], eps[l]) if dual else \
             prox.proj_l2ball(Z[a:b], Yd[a:b], eps[l])
-    assert rel(out, ref) <= TOL[prec]
+    assert_close(out, ref, prec)
     ref_rho = [np.linalg.norm(Z[c["off"][l]:c["off"][l + 1]] - Yd[c["off"][l]:c["off"][l + 1]])
                for l in range(c["L"])]
     np.testing.assert_allclose(host(rho), ref_rho, rtol=1e-12 if prec == "f64" else 1e-6)
