@@ -531,7 +531,8 @@ def run_ours(a):
     cfg = _workload(a.config)
     cfg["tuned"] = {"gram": "tensor cores" if info["gram_tc"] else "CUDA cores",
                     "sweep_rows_per_item": info["sweep_hmax"], "sweep_list_cap": info["sweep_cap"],
-                    "grid_candidates_ms": info["tune_grid_ms"], "tune_s": info["tune_ms"] / 1e3}
+                    "grid_candidates_ms": info["tune_grid_ms"], "fft_adj_chunk": info["fft_adj_chunk"],
+                    "fft_adj_candidates_ms": info["tune_fft_ms"], "tune_s": info["tune_ms"] / 1e3}
     cfg["visibilities"] = M
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -625,17 +626,31 @@ def run_diff(a):
     t_oracle = time.perf_counter() - t0
     gh = g.cpu().numpy().astype(np.float64)
     grad_rel = float(np.linalg.norm(gh - gref) / np.linalg.norm(gref))
+    # central differences need the objective (~1e17 here) to far better than FP32
+    # rounding: they run on an FP64 plan of the same problem, and its gradient
+    # is compared with the FP32 one too
+    from paper_1806_04596_gb300 import hypersara as hs
+    plan64 = hs.Plan(inp.nx, inp.ny, inp.offsets, torch.tensor(uv, dtype=torch.float64, device="cuda"),
+                     levels=4, prec="f64")
+    X64 = X0.double().requires_grad_(True)
+    Y64 = P.y.to(torch.complex128)
+    (g64,) = torch.autograd.grad(ag.objective(plan64, X64, Y64), X64)
     fd = []
     for k in range(2):
-        D = torch.tensor(rng.standard_normal(inp.truth.shape), dtype=torch.float32, device="cuda")
+        D = torch.tensor(rng.standard_normal(inp.truth.shape), dtype=torch.float64, device="cuda")
         with torch.no_grad():
-            fp = float(ag.objective(plan, X0 + 1e-3 * D, P.y).double())
-            fm = float(ag.objective(plan, X0 - 1e-3 * D, P.y).double())
-        fd.append({"fd": (fp - fm) / 2e-3, "grad_dot": float(torch.sum(g.double() * D.double()))})
+            fp = float(ag.objective(plan64, X64.detach() + 1e-3 * D, Y64))
+            fm = float(ag.objective(plan64, X64.detach() - 1e-3 * D, Y64))
+        fd.append({"fd": (fp - fm) / 2e-3, "grad_dot_fp64": float(torch.sum(g64 * D)),
+                   "grad_dot_fp32": float(torch.sum(g.double() * D))})
+    plan64.close()
 
     # unrolled Algorithm 2, gradient of a loss of the final image with respect to y
     eps = P.eps
     unrolled = {}
+    Yw = P.y.clone().requires_grad_(True)   # warm-up (allocator growth, first launches)
+    torch.sum(ag.unrolled_pd(plan, Yw, eps, iters=4, mu=P.mu, kappa3=P.kappa3, checkpoint_every=2)).backward()
+    del Yw
     for ck in (10, 0):
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats()

@@ -80,8 +80,9 @@ typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
 #define HS_PLAN_GRAM_FMA 2u
 /* Keep the default parameters instead of timing candidates at creation. By
  * default a plan times, on itself, the sweep-gridding row cut and list cap
- * ((32, 512), (64, 1024), (128, 2048)) and, for FP32 plans, the tensor-core
- * against the CUDA-core Gram matrix, and keeps the fastest (choices cached per
+ * ((32, 512), (64, 1024), (128, 2048)), F^H over all channels at once against
+ * L2-sized channel chunks and, for FP32 plans, the tensor-core against the
+ * CUDA-core Gram matrix, and keeps the fastest (choices cached per
  * process by grid, L, visibilities, precision and flags; hs_plan_info reports
  * them and the candidate times). */
 #define HS_PLAN_NO_TUNE 4u
@@ -160,6 +161,8 @@ typedef struct {
     double tune_ms;               /* host time spent choosing */
     double tune_grid_ms[3];       /* gridding launch per candidate (32, 64, 128 rows); 0 if not timed */
     double tune_gram_ms[2];       /* Gram matrix: tensor cores, CUDA cores; 0 if not timed */
+    int fft_adj_chunk;            /* channels per F^H chunk (0: all at once) */
+    double tune_fft_ms[2];        /* F^H: all channels, L2-sized chunks; 0 if not timed */
 } hs_plan_info_t;
 
 HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);

@@ -199,6 +199,8 @@ hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info) {
     info->tune_ms = p->tune_ms;
     for (int c = 0; c < 3; ++c) info->tune_grid_ms[c] = p->tune_grid_ms[c];
     for (int c = 0; c < 2; ++c) info->tune_gram_ms[c] = p->tune_gram_ms[c];
+    info->fft_adj_chunk = p->fft_adj_chunk;
+    for (int c = 0; c < 2; ++c) info->tune_fft_ms[c] = p->tune_fft_ms[c];
     return HS_OK;
 }
 

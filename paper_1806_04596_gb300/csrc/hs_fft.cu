@@ -15,6 +15,8 @@
 // Adjoint:      grid --cols, inverse, keep ny rows--> tmp --rows, inverse, crop--> X
 // Only the ny image rows are ever transformed along x: the other Ky - ny rows
 // of Z x are zero in the forward direction and discarded by Z^T in the adjoint.
+#include <algorithm>
+
 #include "hs_device.cuh"
 #include "hs_internal.h"
 
@@ -97,22 +99,24 @@ __device__ __forceinline__ void fft_store(const FftArgs<R>& a, int la, int lb, i
 }
 
 // One Stockham pass of radix RAD (LGR = log2 RAD) over the CTA's G lines:
-// every thread owns 8 / RAD butterflies (8 operands, all in registers).
+// every thread owns NREP x 8 / RAD butterflies (8 NREP operands, all in
+// registers; NREP > 1 lets long column lines come G = 4 to a CTA, so that
+// every 32-byte sector of a column load is used, within 512 threads).
 // LGK_ / LGG_ > 0 fix log2 K and log2 G at compile time (0: from the arguments).
-template <typename R, int DIR, int MODE, int RAD, int LGR, int LGK_, int LGG_>
+template <typename R, int DIR, int MODE, int RAD, int LGR, int LGK_, int LGG_, int NREP>
 __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgNs, bool first,
                                          bool last, int line0) {
     typedef Cx<R> CT;
     constexpr bool COLS = (MODE == COL_FWD || MODE == COL_INV);
-    constexpr int PER = 8 / RAD;
+    constexpr int PER = 8 / RAD * NREP;
     const int lgK = LGK_ > 0 ? LGK_ : a.lgK;
     const int lgG = LGG_ > 0 || LGK_ > 0 ? LGG_ : a.lgG;
     const int K = 1 << lgK, G = 1 << lgG;
-    const int nthr = LGK_ > 0 ? (G << lgK) >> 3 : blockDim.x, tid = threadIdx.x;
+    const int nthr = LGK_ > 0 ? ((G << lgK) >> 3) / NREP : blockDim.x, tid = threadIdx.x;
     const int lgnb = lgK - LGR;
     const int nb = 1 << lgnb;
     const int lgstep = lgK - lgNs - LGR;
-    CT v[8];
+    CT v[8 * NREP];
     int gs[PER], js[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
@@ -187,8 +191,8 @@ __device__ __forceinline__ void fft_pass(const FftArgs<R>& a, Cx<R>* sm, int lgN
 // DIR = -1: forward transform (exp(-2 pi i kn / K)); DIR = +1: unnormalised inverse.
 // LGK_ > 0: K = 2^LGK_ lines of G = 2^LGG_ per CTA fixed at compile time (the
 // pass schedule and every index computation fold to constants); 0: generic.
-template <typename R, int DIR, int MODE, int LGK_, int LGG_>
-__global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 2) k_fft(FftArgs<R> a) {
+template <typename R, int DIR, int MODE, int LGK_, int LGG_, int NREP = 1>
+__global__ void __launch_bounds__(512, NREP > 1 ? 1 : (sizeof(R) == 4 ? 3 : 2)) k_fft(FftArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<R>* sm = reinterpret_cast<Cx<R>*>(smem_raw);
     if constexpr (LGK_ > 0) {
@@ -197,9 +201,9 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 2) k_fft(FftArgs<R> 
 #pragma unroll
         for (int pass = 0; pass < NPASS; ++pass) {
             const bool first = (pass == 0), last = (pass == NPASS - 1);
-            if (pass < N8) fft_pass<R, DIR, MODE, 8, 3, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
-            else if (REM == 2) fft_pass<R, DIR, MODE, 4, 2, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
-            else fft_pass<R, DIR, MODE, 2, 1, LGK_, LGG_>(a, sm, 3 * pass, first, last, line0);
+            if (pass < N8) fft_pass<R, DIR, MODE, 8, 3, LGK_, LGG_, NREP>(a, sm, 3 * pass, first, last, line0);
+            else if (REM == 2) fft_pass<R, DIR, MODE, 4, 2, LGK_, LGG_, NREP>(a, sm, 3 * pass, first, last, line0);
+            else fft_pass<R, DIR, MODE, 2, 1, LGK_, LGG_, NREP>(a, sm, 3 * pass, first, last, line0);
         }
     } else {
         const int line0 = blockIdx.x * a.G;
@@ -207,13 +211,13 @@ __global__ void __launch_bounds__(512, sizeof(R) == 4 ? 3 : 2) k_fft(FftArgs<R> 
         for (int pass = 0; pass < a.npass; ++pass) {
             const bool first = (pass == 0), last = (pass == a.npass - 1);
             if (pass < a.n8) {
-                fft_pass<R, DIR, MODE, 8, 3, 0, 0>(a, sm, lgNs, first, last, line0);
+                fft_pass<R, DIR, MODE, 8, 3, 0, 0, 1>(a, sm, lgNs, first, last, line0);
                 lgNs += 3;
             } else if (a.rlast == 4) {
-                fft_pass<R, DIR, MODE, 4, 2, 0, 0>(a, sm, lgNs, first, last, line0);
+                fft_pass<R, DIR, MODE, 4, 2, 0, 0, 1>(a, sm, lgNs, first, last, line0);
                 lgNs += 2;
             } else {
-                fft_pass<R, DIR, MODE, 2, 1, 0, 0>(a, sm, lgNs, first, last, line0);
+                fft_pass<R, DIR, MODE, 2, 1, 0, 0, 1>(a, sm, lgNs, first, last, line0);
                 lgNs += 1;
             }
         }
@@ -229,8 +233,9 @@ static void radix_plan(int K, int* n8, int* rlast, int* npass) {
     *npass = *n8 + (rem ? 1 : 0);
 }
 
+// nl channels starting at in / out (a channel range of the plan's cube).
 template <typename R, int DIR, int MODE>
-static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) {
+static hs_status launch_fft(Plan* p, const void* in, void* out, int nl, cudaStream_t s) {
     FftArgs<R> a;
     a.in = in;
     a.out = out;
@@ -253,38 +258,54 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
     a.lgK = lg2(K);
     a.lgny = lg2(p->g.ny);
     a.lgKx = lg2(p->g.Kx);
-    int G, nlines;
+    int G, nlines, nrep = 1;
     if (cols) {
-        // 512 threads per CTA so two CTAs share an SM (one loads while the other computes)
+        // 512 threads per CTA so two CTAs share an SM (one loads while the other computes);
+        // lines longer than 1024 come 4 to a CTA (2 for FP64 at 4096: shared memory) with
+        // several butterflies per thread, so column loads use whole 32-byte sectors
         G = 512 / (K / 8);
         if (G > 16) G = 16;
+        if (K >= 2048) {
+            G = (sizeof(R) == 8 && K >= 4096) ? 2 : 4;
+            nrep = G * K / 8 / 512;
+        }
         if (G > p->g.Kx) G = p->g.Kx;
-        nlines = p->g.L * p->g.Kx;
+        nlines = nl * p->g.Kx;
     } else {
         G = 256 / (K / 8);
         if (G < 1) G = 1;
         if (G > p->g.ny) G = p->g.ny;
-        nlines = p->g.L * p->g.ny;
+        nlines = nl * p->g.ny;
     }
     if (G < 1) G = 1;
     a.G = G;
     a.lgG = lg2(G);
-    const int threads = G * K / 8;
+    const int threads = G * K / 8 / nrep;
     const size_t smem = (size_t)G * K * sizeof(Cx<R>);
     const int blocks = nlines / G;
     if (blocks == 0) return HS_OK;
     // compile-time sizes for the common grids (G as chosen above for these K)
 #define HS_FFT_CT(LK, LG) \
-    if (a.lgK == LK && a.lgG == LG) { \
+    if (a.lgK == LK && a.lgG == LG && nrep == 1) { \
         k_fft<R, DIR, MODE, LK, LG><<<blocks, threads, smem, s>>>(a); \
+        HS_CHECK_LAUNCH(); \
+        return HS_OK; \
+    }
+#define HS_FFT_CT_REP(LK, LG, NR) \
+    if (a.lgK == LK && a.lgG == LG && nrep == NR) { \
+        k_fft<R, DIR, MODE, LK, LG, NR><<<blocks, threads, smem, s>>>(a); \
         HS_CHECK_LAUNCH(); \
         return HS_OK; \
     }
     if constexpr (cols) {
         HS_FFT_CT(9, 3)
         HS_FFT_CT(10, 2)
-        HS_FFT_CT(11, 1)
-        HS_FFT_CT(12, 0)
+        HS_FFT_CT_REP(11, 2, 2)
+        if constexpr (sizeof(R) == 4) {
+            HS_FFT_CT_REP(12, 2, 4)
+        } else {
+            HS_FFT_CT_REP(12, 1, 2)
+        }
     } else {
         HS_FFT_CT(9, 2)
         HS_FFT_CT(10, 1)
@@ -292,13 +313,15 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, cudaStream_t s) 
         HS_FFT_CT(12, 0)
     }
 #undef HS_FFT_CT
+#undef HS_FFT_CT_REP
+    if (nrep != 1) return fail(HS_ERR_ARG, "FFT: no kernel for K = %d with %d lines per CTA", K, G);
     k_fft<R, DIR, MODE, 0, 0><<<blocks, threads, smem, s>>>(a);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
 
-template <typename R, int DIR, int MODE, int LK, int LG> static hs_status fft_attr1() {
-    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft<R, DIR, MODE, LK, LG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename R, int DIR, int MODE, int LK, int LG, int NR = 1> static hs_status fft_attr1() {
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft<R, DIR, MODE, LK, LG, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        200 * 1024));
     return HS_OK;
 }
@@ -308,16 +331,31 @@ template <typename R, int DIR, int MODE> static hs_status fft_attr() {
     HS_TRY((fft_attr1<R, DIR, MODE, 0, 0>()));
     HS_TRY((fft_attr1<R, DIR, MODE, 9, cols ? 3 : 2>()));
     HS_TRY((fft_attr1<R, DIR, MODE, 10, cols ? 2 : 1>()));
-    HS_TRY((fft_attr1<R, DIR, MODE, 11, cols ? 1 : 0>()));
-    HS_TRY((fft_attr1<R, DIR, MODE, 12, 0>()));
+    if constexpr (cols) {
+        HS_TRY((fft_attr1<R, DIR, MODE, 11, 2, 2>()));
+        if constexpr (sizeof(R) == 4) {
+            HS_TRY((fft_attr1<R, DIR, MODE, 12, 2, 4>()));
+        } else {
+            HS_TRY((fft_attr1<R, DIR, MODE, 12, 1, 2>()));
+        }
+    } else {
+        HS_TRY((fft_attr1<R, DIR, MODE, 11, 0>()));
+        HS_TRY((fft_attr1<R, DIR, MODE, 12, 0>()));
+    }
     return HS_OK;
 }
 
 // Opt the FFT kernels into large dynamic shared memory (once per process, at
 // plan creation, outside any stream capture).
+static int64_t g_l2_bytes = 0;
+
 hs_status fft_init() {
     static bool done = false;
     if (done) return HS_OK;
+    int dev = 0, l2 = 0;
+    HS_CHECK_CUDA(cudaGetDevice(&dev));
+    HS_CHECK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    g_l2_bytes = l2;
     HS_TRY((fft_attr<float, -1, ROW_FWD>()));
     HS_TRY((fft_attr<float, -1, COL_FWD>()));
     HS_TRY((fft_attr<float, 1, COL_INV>()));
@@ -331,23 +369,45 @@ hs_status fft_init() {
 }
 
 hs_status fft_forward(Plan* p, const void* X, cudaStream_t s) {
+    const int L = p->g.L;
     if (p->prec == HS_F32) {
-        HS_TRY((launch_fft<float, -1, ROW_FWD>(p, X, p->tmp, s)));
-        HS_TRY((launch_fft<float, -1, COL_FWD>(p, p->tmp, p->grid, s)));
+        HS_TRY((launch_fft<float, -1, ROW_FWD>(p, X, p->tmp, L, s)));
+        HS_TRY((launch_fft<float, -1, COL_FWD>(p, p->tmp, p->grid, L, s)));
     } else {
-        HS_TRY((launch_fft<double, -1, ROW_FWD>(p, X, p->tmp, s)));
-        HS_TRY((launch_fft<double, -1, COL_FWD>(p, p->tmp, p->grid, s)));
+        HS_TRY((launch_fft<double, -1, ROW_FWD>(p, X, p->tmp, L, s)));
+        HS_TRY((launch_fft<double, -1, COL_FWD>(p, p->tmp, p->grid, L, s)));
     }
     return HS_OK;
 }
 
+// Channels per adjoint chunk that keep a chunk's traffic within half the L2:
+// the column pass of a chunk streams its grid (Ky Kx cells per channel) and
+// writes the ny x Kx intermediate, which the row pass reads right after, so the
+// intermediate can stay on chip instead of going through HBM and back. More
+// launches, each with a shorter tail: the plan's autotuner keeps the chunked
+// form only where it measures faster (p->fft_adj_chunk, default all channels).
+int fft_adjoint_chunk(const Plan* p) {
+    const int64_t per = ((int64_t)p->g.Ky * p->g.Kx + (int64_t)p->g.ny * p->g.Kx) * (int64_t)p->csize();
+    const int64_t budget = g_l2_bytes > 0 ? g_l2_bytes / 2 : ((int64_t)32 << 20);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(p->g.L, budget / std::max<int64_t>(per, 1)));
+}
+
 hs_status fft_adjoint(Plan* p, void* X, cudaStream_t s) {
-    if (p->prec == HS_F32) {
-        HS_TRY((launch_fft<float, 1, COL_INV>(p, p->grid, p->tmp, s)));
-        HS_TRY((launch_fft<float, 1, ROW_INV>(p, p->tmp, X, s)));
-    } else {
-        HS_TRY((launch_fft<double, 1, COL_INV>(p, p->grid, p->tmp, s)));
-        HS_TRY((launch_fft<double, 1, ROW_INV>(p, p->tmp, X, s)));
+    const int L = p->g.L, C = std::max(1, std::min(L, p->fft_adj_chunk > 0 ? p->fft_adj_chunk : L));
+    const int64_t gch = (int64_t)p->g.Ky * p->g.Kx, tch = (int64_t)p->g.ny * p->g.Kx, xch = p->N();
+    for (int l0 = 0; l0 < L; l0 += C) {
+        const int n = std::min(C, L - l0);
+        if (p->prec == HS_F32) {
+            const float2* g = (const float2*)p->grid + l0 * gch;
+            float2* t = (float2*)p->tmp + l0 * tch;
+            HS_TRY((launch_fft<float, 1, COL_INV>(p, g, t, n, s)));
+            HS_TRY((launch_fft<float, 1, ROW_INV>(p, t, (float*)X + l0 * xch, n, s)));
+        } else {
+            const double2* g = (const double2*)p->grid + l0 * gch;
+            double2* t = (double2*)p->tmp + l0 * tch;
+            HS_TRY((launch_fft<double, 1, COL_INV>(p, g, t, n, s)));
+            HS_TRY((launch_fft<double, 1, ROW_INV>(p, t, (double*)X + l0 * xch, n, s)));
+        }
     }
     return HS_OK;
 }

@@ -138,10 +138,12 @@ struct Plan {
     int gram_tc = 1;                   // FP32 Gram matrix on the tensor cores (else CUDA cores)
     int sweep_hmax = SWEEP_HMAX;       // sweep gridding: most output rows per work item
     int sweep_cap = SWEEP_CAP;         // ... windows above which an item's rows are cut short
+    int fft_adj_chunk = 0;             // channels per F^H chunk (0: all at once)
     int tuned = 0;                     // 1: timed at creation, 2: taken from the process cache
     double tune_ms = 0.0;              // host time spent tuning
     double tune_grid_ms[3] = {0, 0, 0};   // gridding launch time per candidate
     double tune_gram_ms[2] = {0, 0};      // Gram time: tensor cores, CUDA cores
+    double tune_fft_ms[2] = {0, 0};       // F^H time: all channels at once, L2-sized chunks
     void* xbuf = nullptr;              // L * N reals (power iteration, misc)
     void* xbuf2 = nullptr;             // L * N reals
     int64_t device_bytes = 0;
@@ -235,6 +237,8 @@ hs_status nuclear_apply(Plan* p, const void* X, const void* Xadd, const double* 
                         int dual, void* out, double* sv_out, float* warm, int* r_out, cudaStream_t s);
 // S = Z^T Z of Z = X (+ Xadd) into p->gram (L x L, row-major).
 hs_status gram_matrix(Plan* p, const void* X, const void* Xadd, cudaStream_t s);
+// Channels per F^H chunk that fit half the L2 (fft_adjoint below).
+int fft_adjoint_chunk(const Plan* p);
 // Tensor-core Gram matrix of FP32 plans (hs_gram_tc.cu): set-up once per plan
 // creation, the conditions it needs (L <= 64, N a multiple of 64, 16-byte
 // aligned buffers), and the launch writing per-CTA upper-triangle partials

@@ -243,7 +243,9 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
 //     short items balance dense coverage, tall items cut the halo rows;
 //   * FP32 Gram matrix of the nuclear prox on the tensor cores or the CUDA
 //     cores (the tensor-core form streams 64-pixel chunks per SM and wins on
-//     large cubes; the CUDA-core form wins when N L is small).
+//     large cubes; the CUDA-core form wins when N L is small);
+//   * F^H in one column-pass / row-pass pair over all channels, or in channel
+//     chunks sized to keep the intermediate in L2.
 // Choices are cached per process by (grid, L, visibilities, precision, flags),
 // so plans of the same shape skip the timing.
 namespace {
@@ -256,8 +258,8 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int gram_tc, hmax, cap;
-    double grid_ms[3], gram_ms[2];
+    int gram_tc, hmax, cap, fft_chunk;
+    double grid_ms[3], gram_ms[2], fft_ms[2];
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -291,8 +293,10 @@ static hs_status autotune(Plan* p, const std::vector<int>& perm, const std::vect
         if (it != g_tune_cache.end()) {
             const TuneVal& v = it->second;
             p->gram_tc = v.gram_tc;
+            p->fft_adj_chunk = v.fft_chunk;
             std::copy(v.grid_ms, v.grid_ms + 3, p->tune_grid_ms);
             std::copy(v.gram_ms, v.gram_ms + 2, p->tune_gram_ms);
+            std::copy(v.fft_ms, v.fft_ms + 2, p->tune_fft_ms);
             if (sweep && (v.hmax != p->sweep_hmax || v.cap != p->sweep_cap)) {
                 p->sweep_hmax = v.hmax;
                 p->sweep_cap = v.cap;
@@ -335,12 +339,23 @@ static hs_status autotune(Plan* p, const std::vector<int>& perm, const std::vect
         }
         p->gram_tc = p->tune_gram_ms[0] <= p->tune_gram_ms[1];
     }
+    {   // F^H: all channels in one pass pair, or L2-sized channel chunks
+        const int C = fft_adjoint_chunk(p);
+        if (C < L) {
+            p->fft_adj_chunk = 0;
+            HS_TRY(time_ms(s, reps, [&]() { return fft_adjoint(p, p->xbuf, s); }, &p->tune_fft_ms[0]));
+            p->fft_adj_chunk = C;
+            HS_TRY(time_ms(s, reps, [&]() { return fft_adjoint(p, p->xbuf, s); }, &p->tune_fft_ms[1]));
+            if (p->tune_fft_ms[1] >= p->tune_fft_ms[0]) p->fft_adj_chunk = 0;
+        }
+    }
     HS_CHECK_CUDA(cudaStreamSynchronize(s));
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        TuneVal v{p->gram_tc, p->sweep_hmax, p->sweep_cap, {}, {}};
+        TuneVal v{p->gram_tc, p->sweep_hmax, p->sweep_cap, p->fft_adj_chunk, {}, {}, {}};
         std::copy(p->tune_grid_ms, p->tune_grid_ms + 3, v.grid_ms);
         std::copy(p->tune_gram_ms, p->tune_gram_ms + 2, v.gram_ms);
+        std::copy(p->tune_fft_ms, p->tune_fft_ms + 2, v.fft_ms);
         g_tune_cache[key] = v;
     }
     p->tuned = 1;

@@ -43,7 +43,8 @@ class PlanInfo(C.Structure):
                 ("kb_beta", C.c_double), ("kb_fit_max_err", C.c_double),
                 ("device_bytes", C.c_int64), ("nblocks", C.c_int),
                 ("gram_tc", C.c_int), ("sweep_hmax", C.c_int), ("sweep_cap", C.c_int), ("tuned", C.c_int),
-                ("tune_ms", C.c_double), ("tune_grid_ms", C.c_double * 3), ("tune_gram_ms", C.c_double * 2)]
+                ("tune_ms", C.c_double), ("tune_grid_ms", C.c_double * 3), ("tune_gram_ms", C.c_double * 2),
+                ("fft_adj_chunk", C.c_int), ("tune_fft_ms", C.c_double * 2)]
 
 
 class AdaptParams(C.Structure):
