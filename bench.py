@@ -64,6 +64,7 @@ def _args():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--gram", default="", help="n,L: time the Gram matrix alone on an n x n x L cube")
     return ap.parse_args()
 
 
@@ -226,7 +227,8 @@ def synth_L(cfg_id):
 # profiles/stage_traffic.txt together with the SHA-256 of the sources of those
 # kernels: a stage whose sources changed since the capture reports null.
 STAGE_SOURCES = {"fft_fwd": ["hs_fft.cu"], "fft_adj": ["hs_fft.cu"], "degrid": ["hs_nufft.cu", "hs_plan.cpp"],
-                 "grid": ["hs_nufft.cu", "hs_plan.cpp"], "psi_fwd": ["hs_dwt.cu"], "psi_adj": ["hs_dwt.cu"]}
+                 "grid": ["hs_nufft.cu", "hs_plan.cpp"], "psi_fwd": ["hs_dwt.cu"], "psi_adj": ["hs_dwt.cu"],
+                 "gram_tc": ["hs_gram_tc.cu", "hs_prox.cu"], "gram_fma": ["hs_gram_tc.cu", "hs_prox.cu"]}
 
 
 def stage_source_hash(stage: str) -> str:
@@ -412,16 +414,22 @@ def run_ours(a):
                         "limiter": LIMITER[name]}
     if L <= 64:
         Xa = Xo.clone()
-        torch.cuda.nvtx.range_push("stage_gram")
-        g_ms = _events_ms(stream, lambda: plan.gram(Xin, Xa), sreps)
-        torch.cuda.nvtx.range_pop()
+        forms = {}
+        for form, tag in (("tensor_cores", "tc"), ("cuda_cores", "fma")):
+            torch.cuda.nvtx.range_push(f"stage_gram_{tag}")
+            forms[form] = _events_ms(stream, lambda: plan.gram(Xin, Xa, form), sreps)
+            torch.cuda.nvtx.range_pop()
+        g_ms = forms["tensor_cores" if info["gram_tc"] else "cuda_cores"]
         gbs = 8 * NL / (g_ms / 1e3) / 1e9
         stages["gram"] = {"ms": g_ms, "alg_bytes": 8 * NL, "GB_s": gbs, "frac": gbs / hbm,
                           "form": "tensor cores (tcgen05)" if info["gram_tc"] else "CUDA cores",
-                          "tuner_ms": {"tensor_cores": info["tune_gram_ms"][0], "cuda_cores": info["tune_gram_ms"][1]},
+                          "forms_ms": forms,
                           "limiter": LIMITER["gram"] if info["gram_tc"] else "instruction issue (two-sum FMA)"}
     dom = max((k for k in stages if k != "gram"), key=lambda k: stages[k]["ms"])
     traffic = _stage_traffic(dom, a.config)
+    for k in stages:
+        tk = ("gram_tc" if info["gram_tc"] else "gram_fma") if k == "gram" else k
+        stages[k]["traffic"] = _stage_traffic(tk, a.config)
 
     # end to end through the C ABI with host buffers (pinned): y in, X out
     y_host = P.y.cpu().pin_memory()
@@ -770,8 +778,35 @@ def run_precision(a):
     print(json.dumps(line), flush=True)
 
 
+def run_gram(a):
+    """The nuclear prox's Gram matrix alone (hs_gram) on an n x n x L cube
+    Z = X + Xa (the PD form), both forms, CUDA events: `--gram n,L`."""
+    import torch
+    from paper_1806_04596_gb300 import hypersara as hs
+    _gpu_setup()
+    n, L = (int(v) for v in a.gram.split(","))
+    stream = torch.cuda.current_stream()
+    plan = hs.Plan(n, n, np.zeros(L + 1, dtype=np.int64), torch.zeros((0, 2), dtype=torch.float32, device="cuda"),
+                   levels=1, prec="f32")
+    X = torch.rand((L, n, n), dtype=torch.float32, device="cuda")
+    Xa = torch.rand((L, n, n), dtype=torch.float32, device="cuda")
+    hbm, src = _peak_hbm()
+    out = {}
+    for form, tag in (("tensor_cores", "tc"), ("cuda_cores", "fma")):
+        torch.cuda.nvtx.range_push(f"gram_{tag}")
+        ms = _events_ms(stream, lambda: plan.gram(X, Xa, form), max(a.steps, 3))
+        torch.cuda.nvtx.range_pop()
+        gbs = 8.0 * n * n * L / (ms / 1e3) / 1e9
+        out[form] = {"ms": ms, "GB_s": gbs, "frac": gbs / hbm}
+    plan.check()
+    print(json.dumps({"gram": {"n": n, "L": L, "alg_bytes": 8 * n * n * L, "peak_GB_s": hbm, "peak_source": src,
+                               "forms": out}}), flush=True)
+
+
 def main():
     a = _args()
+    if a.gram:
+        return run_gram(a)
     if a.impl == "reference":
         run_reference(a)
     else:

@@ -259,9 +259,10 @@ HS_API hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_
  * CTAs, so |S - S_exact|_ij <~ 1e-7 sqrt(S_ii S_jj). Inputs need |z| < 2^60
  * (else HS_ERR_ARG from hs_plan_check). The CUDA-core form (HS_PLAN_GRAM_FMA,
  * and buffers not 16-byte aligned) sums runs of 32 pixels in FP32 with two-sum
- * compensation. FP64 plans sum in FP64.
+ * compensation. FP64 plans sum in FP64. form: 0 the plan's choice (autotuner),
+ * 1 tensor cores, 2 CUDA cores (FP32 plans; FP64 plans ignore it).
  */
-HS_API hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, double* S_out, void* stream);
+HS_API hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, int form, double* S_out, void* stream);
 
 /*
  * hs_proj_l2ball - per-channel projection onto B(y_l, eps_l) =

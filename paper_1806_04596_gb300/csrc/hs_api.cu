@@ -296,15 +296,20 @@ hs_status hs_prox_nuclear(hs_plan_t plan, const void* X, const double* w_sv, dou
                          S(stream));
 }
 
-hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, double* S_out, void* stream) {
+hs_status hs_gram(hs_plan_t plan, const void* X, const void* Xadd, int form, double* S_out, void* stream) {
     clear_error();
     CHECK_PLAN(plan);
     if (X == nullptr || S_out == nullptr) return fail(HS_ERR_ARG, "hs_gram: null buffer");
+    if (form < 0 || form > 2) return fail(HS_ERR_ARG, "hs_gram: form must be 0, 1 or 2");
     Plan* p = plan->p;
     const int L = p->g.L;
     if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "hs_gram: L = %d exceeds %d", L, MAX_L_NUC);
     cudaStream_t s = S(stream);
-    HS_TRY(gram_matrix(p, X, Xadd, s));
+    const int keep = p->gram_tc;
+    if (form) p->gram_tc = form == 1;
+    const hs_status st = gram_matrix(p, X, Xadd, s);
+    p->gram_tc = keep;
+    HS_TRY(st);
     HS_CHECK_CUDA(cudaMemcpyAsync(S_out, p->gram, (size_t)L * L * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return HS_OK;
 }

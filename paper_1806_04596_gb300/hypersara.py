@@ -80,7 +80,7 @@ _SIGS = {
     "hs_prox_l21": ([_P, _P, _P, C.c_double, C.c_int, _P, _P], C.c_int),
     "hs_prox_nuclear": ([_P, _P, _P, C.c_double, C.c_int, _P, _P, _P], C.c_int),
     "hs_l21_grad": ([_P, _P, _P, _P, _P], C.c_int),
-    "hs_gram": ([_P, _P, _P, _P, _P], C.c_int),
+    "hs_gram": ([_P, _P, _P, C.c_int, _P, _P], C.c_int),
     "hs_proj_l2ball": ([_P, _P, _P, _P, C.c_int, _P, _P, _P], C.c_int),
     "hs_proj_l2ball_static": ([C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P], C.c_int),
     "hs_norm_l21": ([_P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
@@ -381,12 +381,14 @@ class Plan:
                                                          _stream()))
         return out, sv
 
-    def gram(self, X, Xadd=None):
-        """hs_gram: the L x L Gram matrix of the cube X (+ Xadd), FP64 CUDA tensor."""
+    def gram(self, X, Xadd=None, form: str = "plan"):
+        """hs_gram: the L x L Gram matrix of the cube X (+ Xadd), FP64 CUDA tensor.
+        form: "plan" (the autotuner's choice), "tensor_cores" or "cuda_cores"."""
         torch = _torch()
+        f = {"plan": 0, "tensor_cores": 1, "cuda_cores": 2}[form]
         pX, pA = _args(self._img(X, "X"), self._img(Xadd, "Xadd") + (True,))
         S = torch.empty((self.L, self.L), dtype=torch.float64, device="cuda")
-        _check("hs_gram", load().hs_gram(self.h, pX, pA, _ptr(S), _stream()))
+        _check("hs_gram", load().hs_gram(self.h, pX, pA, f, _ptr(S), _stream()))
         return S
 
     def proj_l2ball(self, Z, Yd, eps, dual: bool = False, out=None):
