@@ -506,8 +506,9 @@ HS_API hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_e
  * Rows of an item are cut after hmax rows, or earlier once its list would pass
  * cap windows (hmax, cap <= 0: the defaults 64 and 1024; the autotuner of
  * hs_plan_create chooses among (32, 512), (64, 1024) and (128, 2048)).
- * Errors: HS_ERR_ARG for non-power-of-two or small grids, bad offsets, start
- * cells outside the grid, or short buffers.
+ * Errors: HS_ERR_ARG for grids narrower than 64 or not a multiple of 32
+ * (columns) or 8 (rows), bad offsets, start cells outside the grid, or short
+ * buffers.
  */
 HS_API hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y,
                                 int hmax, int cap, int* items, int64_t* n_items, int* ent, int64_t* n_ent);

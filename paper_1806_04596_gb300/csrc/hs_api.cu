@@ -94,9 +94,9 @@ hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err) {
 hs_status hs_sweep_lists(int Kx, int Ky, int L, const int64_t* offsets, const int* k0x, const int* k0y, int hmax,
                          int cap, int* items, int64_t* n_items, int* ent, int64_t* n_ent) {
     clear_error();
-    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-    if (!pow2(Kx) || !pow2(Ky) || Kx < 2 * hs::GRID_TILE || Ky < 2 * hs::GRID_TILE)
-        return fail(HS_ERR_ARG, "hs_sweep_lists: Kx, Ky must be powers of two >= %d", 2 * hs::GRID_TILE);
+    if (Kx % hs::GRID_TILE || Ky % 8 || Kx < 2 * hs::GRID_TILE || Ky < 2 * hs::GRID_TILE)
+        return fail(HS_ERR_ARG, "hs_sweep_lists: Kx must be a multiple of %d and Ky of 8, both >= %d", hs::GRID_TILE,
+                    2 * hs::GRID_TILE);
     if (L < 1 || offsets == nullptr || n_items == nullptr || n_ent == nullptr || offsets[0] != 0)
         return fail(HS_ERR_ARG, "hs_sweep_lists: need L >= 1, offsets from 0 and the count pointers");
     for (int l = 0; l < L; ++l)

@@ -90,6 +90,18 @@ template <typename R, int NC> __device__ __forceinline__ R horner(const R* c, R 
     return v;
 }
 
+// x mod n for x in [-n, 2n): with m = n - 1 (n a power of two) the mask, with
+// m < 0 (any other n) one conditional correction each way. m is uniform
+// across a launch, so the choice never diverges.
+__device__ __forceinline__ int wrapn(int x, int n, int m) {
+    if (m >= 0) return x & m;
+    x += x < 0 ? n : 0;
+    return x >= n ? x - n : x;
+}
+
+// The wrap mask of wrapn for a period n.
+__host__ __device__ __forceinline__ int wrap_mask(int n) { return (n & (n - 1)) == 0 ? n - 1 : -1; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

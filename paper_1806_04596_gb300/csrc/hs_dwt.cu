@@ -82,23 +82,36 @@ __device__ __forceinline__ void st4(double* p, double a, double b, double c, dou
     reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
 }
 
-// Stages rows [y0, y0 + ry) x columns [x0, x0 + rx) of a periodic block (indices
-// wrapped with the power-of-two masks) into in[r * SIN + c].
+// x mod n for x in [-n, 2n): the mask when every level of the image is a power
+// of two (P2, the common case, a compile-time choice), else one conditional
+// correction each way (sides 3 or 5 times a power of two).
+template <bool P2> __device__ __forceinline__ int wrapp(int x, int n) {
+    if constexpr (P2) {
+        return x & (n - 1);
+    } else {
+        x += x < 0 ? n : 0;
+        return x >= n ? x - n : x;
+    }
+}
+
+// Stages rows [y0, y0 + ry) x columns [x0, x0 + rx) of a periodic ysz x xsz
+// block (indices wrapped with wrapp; y0, x0 >= 0 and the region shorter than
+// the block) into in[r * SIN + c].
 // FP32 with an 8-byte aligned block (`pairs`): x0, rx and the block width are
 // even, so columns move as 8-byte pairs that never straddle the periodic wrap.
-template <typename R>
-__device__ __forceinline__ void stage_region(R* in, const R* __restrict__ base, int64_t stride, int ymask,
-                                             int xmask, int y0, int x0, int ry, int rx, bool pairs) {
+template <typename R, bool P2>
+__device__ __forceinline__ void stage_region(R* in, const R* __restrict__ base, int64_t stride, int ysz,
+                                             int xsz, int y0, int x0, int ry, int rx, bool pairs) {
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     if (sizeof(R) == 4 && pairs) {
         for (int r = wy; r < ry; r += 8) {
-            const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
-            for (int c = 2 * lane; c < rx; c += 64) cp_async8(in + r * SIN + c, row + ((x0 + c) & xmask));
+            const R* row = base + (int64_t)wrapp<P2>(y0 + r, ysz) * stride;
+            for (int c = 2 * lane; c < rx; c += 64) cp_async8(in + r * SIN + c, row + wrapp<P2>(x0 + c, xsz));
         }
     } else {
         for (int r = wy; r < ry; r += 8) {
-            const R* row = base + (int64_t)((y0 + r) & ymask) * stride;
-            for (int c = lane; c < rx; c += 32) cp_async(in + r * SIN + c, row + ((x0 + c) & xmask));
+            const R* row = base + (int64_t)wrapp<P2>(y0 + r, ysz) * stride;
+            for (int c = lane; c < rx; c += 32) cp_async(in + r * SIN + c, row + wrapp<P2>(x0 + c, xsz));
         }
     }
     cp_async_commit();
@@ -205,7 +218,7 @@ template <typename R, int D> __device__ __forceinline__ void fwd_all(const FwdCt
 // Level 0 of Psi^dagger for one (output tile, channel): the Dirac block
 // A[0] = X / 3 and the first level of all 8 wavelets. LL goes to the compact
 // buffer ll_out (stride nx / 2), or to A[1+d] when there is a single level.
-template <typename R>
+template <typename R, bool P2>
 __global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* __restrict__ A,
                                                    R* __restrict__ ll_out, int L, int ny, int nx, int last,
                                                    R sc, int pairs) {
@@ -219,7 +232,7 @@ __global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* 
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int k0y = ty * qy, k0x = tx * qx;
     const int64_t N = (int64_t)ny * nx;
-    stage_region(in, X + l * N, nx, ny - 1, nx - 1, 2 * k0y, 2 * k0x, 2 * qy + MAXF - 2, 2 * qx + MAXF - 2,
+    stage_region<R, P2>(in, X + l * N, nx, ny, nx, 2 * k0y, 2 * k0x, 2 * qy + MAXF - 2, 2 * qx + MAXF - 2,
                  pairs != 0);
     cp_async_wait<0>();
     __syncthreads();
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(256) k_psi_fwd_l0(const R* __restrict__ X, R* 
 // One analysis level > 0 for every (wavelet d, channel l): input the previous
 // level's LL (compact my x mx in `src`); details to A[1+d] at their Mallat
 // positions, LL to `ll_out` (compact) or to A[1+d] at the last level.
-template <typename R>
+template <typename R, bool P2>
 __global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ src, R* __restrict__ A,
                                                       R* __restrict__ ll_out, int L, int ny, int nx, int my,
                                                       int mx, int last) {
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(256) k_dwt_fwd_level(const R* __restrict__ src
 #define HS_FWD(DD)                                                                                       \
     {                                                                                                    \
         constexpr int F = 2 * (DD + 1);                                                                  \
-        stage_region(in, base, mx, my - 1, mx - 1, 2 * k0y, 2 * k0x, 2 * qy + F - 2, 2 * qx + F - 2, true); \
+        stage_region<R, P2>(in, base, mx, my, mx, 2 * k0y, 2 * k0x, 2 * qy + F - 2, 2 * qx + F - 2, true); \
         cp_async_wait<0>();                                                                              \
         __syncthreads();                                                                                 \
         fwd_rows<R, DD>(in, ro, 2 * qy + F - 2, qx);                                                     \
@@ -279,7 +292,7 @@ template <typename R, int D> __host__ __device__ constexpr int inv_co() {
 // subband 0 (LL) comes from `ll` (row stride lls). With 16-byte aligned
 // coefficients (`chunks`), subbands at least one 16-byte chunk wide move in
 // aligned chunks (which never straddle the wrap).
-template <typename R, int CO>
+template <typename R, int CO, bool P2>
 __device__ __forceinline__ void inv_stage(R* cf, const R* __restrict__ Ad, const R* __restrict__ ll,
                                           int64_t lls, int nx, int hy, int hx, int ky0, int kx0, int cyn,
                                           int cxn, bool chunks) {
@@ -289,23 +302,23 @@ __device__ __forceinline__ void inv_stage(R* cf, const R* __restrict__ Ad, const
     if (chunks && hx >= EPC) {
         const int nch = (cxn + CO + EPC - 1) / EPC;
         const int cc = lane % LPR, rr = lane / LPR;
-        const int gx = (kx0 - CO + EPC * cc) & (hx - 1);
+        const int gx = wrapp<P2>(kx0 - CO + EPC * cc, hx);
         if (cc < nch) {
 #pragma unroll
             for (int s = 0; s < 4; ++s)
                 for (int yy = (32 / LPR) * wy + rr; yy < cyn; yy += 8 * (32 / LPR)) {
-                    const int gy = (ky0 + yy) & (hy - 1);
+                    const int gy = wrapp<P2>(ky0 + yy, hy);
                     const R* src = (s == 0) ? ll + (int64_t)gy * lls + gx
                                             : Ad + (int64_t)((s >> 1) * hy + gy) * nx + (s & 1) * hx + gx;
                     cp_async16(cf + (s * DC + yy) * SCS + EPC * cc, src);
                 }
         }
     } else if (lane < cxn) {
-        const int gx = (kx0 + lane) & (hx - 1);
+        const int gx = wrapp<P2>(kx0 + lane, hx);
 #pragma unroll
         for (int s = 0; s < 4; ++s)
             for (int yy = wy; yy < cyn; yy += 8) {
-                const int gy = (ky0 + yy) & (hy - 1);
+                const int gy = wrapp<P2>(ky0 + yy, hy);
                 const R* src = (s == 0) ? ll + (int64_t)gy * lls + gx
                                         : Ad + (int64_t)((s >> 1) * hy + gy) * nx + (s & 1) * hx + gx;
                 cp_async(cf + (s * DC + yy) * SCS + CO + lane, src);
@@ -402,7 +415,7 @@ __device__ __forceinline__ void tile_store(R* T, const R* acc, R* __restrict__ o
 // One synthesis level > 0 for every (d, l): reconstructs the my x mx block
 // (compact, stride mx, into `out`) from its LL (`llbuf`: A[1+d] at the coarsest
 // level, else the coarser level's output, compact stride mx / 2) and A[1+d].
-template <typename R>
+template <typename R, bool P2>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
     k_dwt_inv_level(const R* __restrict__ A, const R* __restrict__ llbuf,
                     int ll_from_a, R* __restrict__ out, int L, int ny,
@@ -423,7 +436,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
 #define HS_INV(DD)                                                                                   \
     {                                                                                                \
         constexpr int H = DD + 1;                                                                    \
-        inv_stage<R, inv_co<R, DD>()>(cf, Ad, ll, lls, nx, hy, hx, ty * qy - (H - 1),                \
+        inv_stage<R, inv_co<R, DD>(), P2>(cf, Ad, ll, lls, nx, hy, hx, ty * qy - (H - 1),            \
                                       tx * qx - (H - 1), qy + H - 1, qx + H - 1, chunks != 0);       \
         cp_async_wait<0>();                                                                          \
         __syncthreads();                                                                             \
@@ -447,21 +460,21 @@ template <typename R> struct InvCtx {
     int L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a, chunks;
 };
 
-template <typename R, int D> __device__ __forceinline__ void inv_stage_d(const InvCtx<R>& c) {
+template <typename R, int D, bool P2> __device__ __forceinline__ void inv_stage_d(const InvCtx<R>& c) {
     constexpr int H = D + 1;
     const R* Ad = c.A + ((int64_t)(1 + D) * c.L + c.l) * c.N;
     const R* ll = c.ll_from_a ? Ad : c.llbuf + ((int64_t)D * c.L + c.l) * (int64_t)c.hy * c.hx;
-    inv_stage<R, inv_co<R, D>()>(c.cf + (D & 1) * 4 * DC * SCS, Ad, ll, c.ll_from_a ? c.nx : c.hx, c.nx, c.hy,
+    inv_stage<R, inv_co<R, D>(), P2>(c.cf + (D & 1) * 4 * DC * SCS, Ad, ll, c.ll_from_a ? c.nx : c.hx, c.nx, c.hy,
                                  c.hx, c.ty * c.qy - (H - 1), c.tx * c.qx - (H - 1), c.qy + H - 1, c.qx + H - 1,
                                  c.chunks != 0);
 }
 
 // Level-0 synthesis of all eight wavelets, the next wavelet's subbands staged
 // while the current one is filtered.
-template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCtx<R>& c, R* acc) {
+template <typename R, int D, bool P2> __device__ __forceinline__ void inv_all(const InvCtx<R>& c, R* acc) {
     if constexpr (D < NW) {
         if constexpr (D + 1 < NW) {
-            inv_stage_d<R, D + 1>(c);
+            inv_stage_d<R, D + 1, P2>(c);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -470,13 +483,13 @@ template <typename R, int D> __device__ __forceinline__ void inv_all(const InvCt
         inv_cols<R, D>(c.cf + (D & 1) * 4 * DC * SCS, c.cl, c.qy, c.qx + D);
         __syncthreads();
         inv_rows<R, D>(c.cl, acc, c.qy, c.qx);
-        inv_all<R, D + 1>(c, acc);
+        inv_all<R, D + 1, P2>(c, acc);
     }
 }
 
 // Level-0 synthesis summed over the 9 bases: X[l] = (A[0][l] + sum_d W_d^T A[1+d][l]) / 3,
 // one CTA per (output tile, channel).
-template <typename R>
+template <typename R, bool P2>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
     k_psi_adj_l0(const R* __restrict__ A, const R* __restrict__ llbuf,
                  int ll_from_a, R* __restrict__ X, int L, int ny, int nx,
@@ -491,9 +504,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
     const int ty = blockIdx.x / ntx, tx = blockIdx.x - ty * ntx;
     const int64_t N = (int64_t)ny * nx;
     InvCtx<R> c{cf, cl, A, llbuf, N, L, l, nx, hy, hx, ty, tx, qy, qx, ll_from_a, chunks};
-    inv_stage_d<R, 0>(c);
+    inv_stage_d<R, 0, P2>(c);
     R acc[4] = {0, 0, 0, 0};
-    inv_all<R, 0>(c, acc);
+    inv_all<R, 0, P2>(c, acc);
     __syncthreads();
     const int64_t t0 = (int64_t)(2 * ty * qy) * nx + 2 * tx * qx;
     tile_store<R>(cl, acc, X + l * N + t0, A + l * N + t0, nx, qy, qx, s);
@@ -528,14 +541,22 @@ template <typename K> static hs_status smem_attr(K k, int bytes) {
 
 hs_status dwt_init() {
     HS_TRY(upload_filters());
-    HS_TRY(smem_attr(k_psi_fwd_l0<float>, FWD_SMEM * 4));
-    HS_TRY(smem_attr(k_psi_fwd_l0<double>, FWD_SMEM * 8));
-    HS_TRY(smem_attr(k_dwt_fwd_level<float>, FWD_SMEM * 4));
-    HS_TRY(smem_attr(k_dwt_fwd_level<double>, FWD_SMEM * 8));
-    HS_TRY(smem_attr(k_dwt_inv_level<float>, INV_SMEM * 4));
-    HS_TRY(smem_attr(k_dwt_inv_level<double>, INV_SMEM * 8));
-    HS_TRY(smem_attr(k_psi_adj_l0<float>, INV_SMEM * 4));
-    HS_TRY(smem_attr(k_psi_adj_l0<double>, INV_SMEM * 8));
+    HS_TRY(smem_attr(k_psi_fwd_l0<float, true>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_fwd_l0<double, true>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_fwd_level<float, true>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_fwd_level<double, true>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_inv_level<float, true>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_inv_level<double, true>, INV_SMEM * 8));
+    HS_TRY(smem_attr(k_psi_adj_l0<float, true>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_adj_l0<double, true>, INV_SMEM * 8));
+    HS_TRY(smem_attr(k_psi_fwd_l0<float, false>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_fwd_l0<double, false>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_fwd_level<float, false>, FWD_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_fwd_level<double, false>, FWD_SMEM * 8));
+    HS_TRY(smem_attr(k_dwt_inv_level<float, false>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_dwt_inv_level<double, false>, INV_SMEM * 8));
+    HS_TRY(smem_attr(k_psi_adj_l0<float, false>, INV_SMEM * 4));
+    HS_TRY(smem_attr(k_psi_adj_l0<double, false>, INV_SMEM * 8));
     return HS_OK;
 }
 
@@ -545,25 +566,25 @@ static inline unsigned ntiles(int my, int mx) {
     return (unsigned)((hy / qy) * (hx / qx));
 }
 
-template <typename R> static hs_status analysis_t(Plan* p, const R* X, R* A, cudaStream_t s) {
+template <typename R, bool P2> static hs_status analysis_t(Plan* p, const R* X, R* A, cudaStream_t s) {
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
     const int top = p->levels - 1;
     const int pairs = ((uintptr_t)X % 8) == 0;   // caller's image: 8-byte pairs only when aligned
-    k_psi_fwd_l0<R><<<dim3(ntiles(ny, nx), L), 256, FWD_SMEM * sizeof(R), s>>>(X, A, buf[0], L, ny, nx, top == 0,
+    k_psi_fwd_l0<R, P2><<<dim3(ntiles(ny, nx), L), 256, FWD_SMEM * sizeof(R), s>>>(X, A, buf[0], L, ny, nx, top == 0,
                                                                               (R)(1.0 / 3.0), pairs);
     HS_CHECK_LAUNCH();
     for (int lev = 1; lev <= top; ++lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
-        k_dwt_fwd_level<R><<<g, 256, FWD_SMEM * sizeof(R), s>>>(buf[(lev - 1) & 1], A, buf[lev & 1], L, ny, nx,
+        k_dwt_fwd_level<R, P2><<<g, 256, FWD_SMEM * sizeof(R), s>>>(buf[(lev - 1) & 1], A, buf[lev & 1], L, ny, nx,
                                                                 my, mx, lev == top);
         HS_CHECK_LAUNCH();
     }
     return HS_OK;
 }
 
-template <typename R> static hs_status synthesis_t(Plan* p, const R* A, R* X, cudaStream_t s) {
+template <typename R, bool P2> static hs_status synthesis_t(Plan* p, const R* A, R* X, cudaStream_t s) {
     const int chunks = ((uintptr_t)A % 16) == 0;   // caller's coefficients: 16-byte chunks only when aligned
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
@@ -571,25 +592,35 @@ template <typename R> static hs_status synthesis_t(Plan* p, const R* A, R* X, cu
     for (int lev = top; lev >= 1; --lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
-        k_dwt_inv_level<R><<<g, 256, INV_SMEM * sizeof(R), s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1],
+        k_dwt_inv_level<R, P2><<<g, 256, INV_SMEM * sizeof(R), s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1],
                                                                 lev == top, buf[lev & 1], L, ny, nx, my, mx,
                                                                 chunks);
         HS_CHECK_LAUNCH();
     }
-    k_psi_adj_l0<R><<<dim3(ntiles(ny, nx), L), 256, INV_SMEM * sizeof(R), s>>>(
+    k_psi_adj_l0<R, P2><<<dim3(ntiles(ny, nx), L), 256, INV_SMEM * sizeof(R), s>>>(
         A, top == 0 ? nullptr : buf[1], top == 0, X, L, ny, nx, (R)(1.0 / 3.0), chunks);
     HS_CHECK_LAUNCH();
     return HS_OK;
 }
 
+static bool pow2_image(const Plan* p) { return wrap_mask(p->g.nx) >= 0 && wrap_mask(p->g.ny) >= 0; }
+
 hs_status dwt_analysis(Plan* p, const void* X, void* A, cudaStream_t s) {
-    if (p->prec == HS_F32) return analysis_t<float>(p, (const float*)X, (float*)A, s);
-    return analysis_t<double>(p, (const double*)X, (double*)A, s);
+    const bool p2 = pow2_image(p);
+    if (p->prec == HS_F32)
+        return p2 ? analysis_t<float, true>(p, (const float*)X, (float*)A, s)
+                  : analysis_t<float, false>(p, (const float*)X, (float*)A, s);
+    return p2 ? analysis_t<double, true>(p, (const double*)X, (double*)A, s)
+              : analysis_t<double, false>(p, (const double*)X, (double*)A, s);
 }
 
 hs_status dwt_synthesis(Plan* p, const void* A, void* X, cudaStream_t s) {
-    if (p->prec == HS_F32) return synthesis_t<float>(p, (const float*)A, (float*)X, s);
-    return synthesis_t<double>(p, (const double*)A, (double*)X, s);
+    const bool p2 = pow2_image(p);
+    if (p->prec == HS_F32)
+        return p2 ? synthesis_t<float, true>(p, (const float*)A, (float*)X, s)
+                  : synthesis_t<float, false>(p, (const float*)A, (float*)X, s);
+    return p2 ? synthesis_t<double, true>(p, (const double*)A, (double*)X, s)
+              : synthesis_t<double, false>(p, (const double*)A, (double*)X, s);
 }
 
 }  // namespace hs

@@ -15,6 +15,12 @@
 // Adjoint:      grid --cols, inverse, keep ny rows--> tmp --rows, inverse, crop--> X
 // Only the ny image rows are ever transformed along x: the other Ky - ny rows
 // of Z x are zero in the forward direction and discarded by Z^T in the adjoint.
+//
+// Lines whose length is not a power of two (K = r 2^m, r = 3 or 5: images
+// such as 1280 x 1280, grids of 2560) use k_fft_mr: the same gather / scatter
+// modes around a mixed-radix Stockham schedule (one radix-r pass, then radix
+// 4 and 2) with each pass's small DFT evaluated directly, ping-ponging between
+// two shared-memory copies of the CTA's lines.
 #include <algorithm>
 
 #include "hs_device.cuh"
@@ -224,6 +230,117 @@ __global__ void __launch_bounds__(512, NREP > 1 ? 1 : (sizeof(R) == 4 ? 3 : 2)) 
     }
 }
 
+// ---------------------------------------------------------------- mixed radix (K = r 2^m)
+constexpr int MR_MAXPASS = 16;
+struct MrPlan {
+    int npass;
+    int radix[MR_MAXPASS];
+};
+
+// Line index -> (channel, row or column), any K.
+template <int MODE>
+__device__ __forceinline__ void line_of_any(int line, int Kx, int ny, int& la, int& lb) {
+    if (MODE == COL_FWD || MODE == COL_INV) {
+        la = line / Kx;
+        lb = line - la * Kx;
+    } else {
+        la = line / ny;
+        lb = line - la * ny;
+    }
+}
+
+// Self-sorting Stockham transform of G lines of length K = prod(radix) held in
+// shared memory: pass with radix q and sub-transform length Ns reads
+// x_t = in[j + t K/q] (t < q), multiplies by w_{Ns q}^{t (j mod Ns)}, takes the
+// q-point DFT and writes it to out[(j / Ns) Ns q + (j mod Ns) + u Ns] (u < q);
+// after all passes the lines are in natural order. Twiddles come from the
+// K-point table w^m = exp(-2 pi i m / K) (conjugated for DIR = +1).
+template <typename R, int DIR, int MODE>
+__global__ void __launch_bounds__(512) k_fft_mr(FftArgs<R> a, MrPlan mp) {
+    typedef Cx<R> CT;
+    constexpr bool COLS = (MODE == COL_FWD || MODE == COL_INV);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K = a.K, G = a.G, GK = G * K;
+    CT* src = reinterpret_cast<CT*>(smem_raw);
+    CT* dst = src + GK;
+    const int line0 = blockIdx.x * G, tid = threadIdx.x, nthr = blockDim.x;
+    for (int e = tid; e < GK; e += nthr) {   // consecutive threads: consecutive columns / row elements
+        const int g = COLS ? e % G : e / K, k = COLS ? e / G : e % K;
+        int la, lb;
+        line_of_any<MODE>(line0 + g, a.Kx, a.ny, la, lb);
+        src[g * K + k] = fft_load<R, MODE>(a, la, lb, k);
+    }
+    __syncthreads();
+    auto tw = [&](int m) {
+        CT t = a.tw[m];
+        if (DIR > 0) t.y = -t.y;
+        return t;
+    };
+    int Ns = 1;
+    for (int pass = 0; pass < mp.npass; ++pass) {
+        const int q = mp.radix[pass], nb = K / q, step = K / q;
+        for (int e = tid; e < G * nb; e += nthr) {
+            const int g = e / nb, j = e - g * nb;
+            const int k = j % Ns;
+            CT x[5], y[5];
+#pragma unroll
+            for (int t = 0; t < 5; ++t)
+                if (t < q) x[t] = src[g * K + j + t * nb];
+            if (Ns > 1) {
+                const int tstep = K / (Ns * q);
+#pragma unroll
+                for (int t = 1; t < 5; ++t)
+                    if (t < q) x[t] = cmul(x[t], tw(t * k * tstep));
+            }
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+                if (u >= q) break;
+                CT acc = x[0];
+#pragma unroll
+                for (int t = 1; t < 5; ++t)
+                    if (t < q) acc = cadd(acc, cmul(x[t], tw(((u * t) % q) * step)));
+                y[u] = acc;
+            }
+            const int base = (j / Ns) * Ns * q + k;
+#pragma unroll
+            for (int u = 0; u < 5; ++u)
+                if (u < q) dst[g * K + base + u * Ns] = y[u];
+        }
+        __syncthreads();
+        CT* t = src;
+        src = dst;
+        dst = t;
+        Ns *= q;
+    }
+    for (int e = tid; e < GK; e += nthr) {
+        const int g = COLS ? e % G : e / K, k = COLS ? e / G : e % K;
+        int la, lb;
+        line_of_any<MODE>(line0 + g, a.Kx, a.ny, la, lb);
+        fft_store<R, MODE>(a, la, lb, k, src[g * K + k]);
+    }
+}
+
+static bool mr_plan(int K, MrPlan* mp) {
+    mp->npass = 0;
+    for (int r : {5, 3}) {
+        if (K % r == 0) {
+            mp->radix[mp->npass++] = r;
+            K /= r;
+        }
+    }
+    while (K % 4 == 0 && mp->npass < MR_MAXPASS) {
+        mp->radix[mp->npass++] = 4;
+        K /= 4;
+    }
+    if (K == 2 && mp->npass < MR_MAXPASS) {
+        mp->radix[mp->npass++] = 2;
+        K = 1;
+    }
+    return K == 1;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
 static void radix_plan(int K, int* n8, int* rlast, int* npass) {
     int p = 0;
     while ((1 << p) < K) ++p;
@@ -249,6 +366,23 @@ static hs_status launch_fft(Plan* p, const void* in, void* out, int nl, cudaStre
     const int K = cols ? p->g.Ky : p->g.Kx;
     a.K = K;
     a.tw = (const Cx<R>*)(cols ? p->twy : p->twx);
+    if (!is_pow2(K) || !is_pow2(cols ? p->g.Kx : p->g.ny)) {   // mixed radix, generic indexing
+        MrPlan mp;
+        if (!mr_plan(K, &mp)) return fail(HS_ERR_ARG, "FFT: line length %d is not r 2^m with r in {1, 3, 5}", K);
+        int G = 1;
+        if (cols) {   // whole 32-byte sectors per column load where shared memory allows
+            const int want = (int)(32 / sizeof(Cx<R>)) > 0 ? (int)(32 / sizeof(Cx<R>)) : 1;
+            G = std::max(1, want);
+            while (G > 1 && (p->g.Kx % G != 0 || (size_t)2 * G * K * sizeof(Cx<R>) > (size_t)200 * 1024)) G >>= 1;
+        }
+        a.G = G;
+        const int nlines = nl * (cols ? p->g.Kx : p->g.ny);
+        const size_t smem = (size_t)2 * G * K * sizeof(Cx<R>);
+        if (smem > (size_t)200 * 1024) return fail(HS_ERR_ARG, "FFT: line length %d too long", K);
+        k_fft_mr<R, DIR, MODE><<<nlines / G, 512, smem, s>>>(a, mp);
+        HS_CHECK_LAUNCH();
+        return HS_OK;
+    }
     radix_plan(K, &a.n8, &a.rlast, &a.npass);
     auto lg2 = [](int v) {
         int r = 0;
@@ -328,6 +462,8 @@ template <typename R, int DIR, int MODE, int LK, int LG, int NR = 1> static hs_s
 
 template <typename R, int DIR, int MODE> static hs_status fft_attr() {
     constexpr bool cols = (MODE == COL_FWD || MODE == COL_INV);
+    HS_CHECK_CUDA(cudaFuncSetAttribute(k_fft_mr<R, DIR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024));
     HS_TRY((fft_attr1<R, DIR, MODE, 0, 0>()));
     HS_TRY((fft_attr1<R, DIR, MODE, 9, cols ? 3 : 2>()));
     HS_TRY((fft_attr1<R, DIR, MODE, 10, cols ? 2 : 1>()));

@@ -75,6 +75,7 @@ struct Geo {
     int nx, ny, L, Kx, Ky;
     int fbx, fby;          // fractional bits of the FP32 fixed-point coordinates
     int tx, ty, ntx, nty;  // gridding tile size and tiles per axis
+    int kxm, kym;          // Kx - 1, Ky - 1 for powers of two, else -1 (wrapn)
 };
 
 // ---------------------------------------------------------------- plan

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1)
     const int l = it.tix / ntiles;
     const int t = it.tix - l * ntiles;
     const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int kxm = a.g.kxm, kym = a.g.kym;
     const int ty0 = (t / a.g.ntx) * a.g.ty, tx0 = (t % a.g.ntx) * a.g.tx;
     const CT* G = a.grid + (int64_t)l * Ky * Kx;
     if constexpr (sizeof(R) == 4) {
@@ -117,13 +118,13 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1)
         for (int k = threadIdx.x; k < DG_REG * CPR; k += blockDim.x) {
             const int r = k / CPR, c = 2 * (k - r * CPR);
             const unsigned d = (unsigned)__cvta_generic_to_shared(S + r * DG_LDS + c);
-            const CT* src = G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1));
+            const CT* src = G + (int64_t)(wrapn(ty0 + r, Ky, kym)) * Kx + (wrapn(tx0 + c, Kx, kxm));
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
         }
     } else {
         for (int k = threadIdx.x; k < DG_REG * DG_REG; k += blockDim.x) {
             const int r = k / DG_REG, c = k - r * DG_REG;
-            cp_async_cx<R>(S + r * DG_LDS + c, G + (int64_t)((ty0 + r) & (Ky - 1)) * Kx + ((tx0 + c) & (Kx - 1)));
+            cp_async_cx<R>(S + r * DG_LDS + c, G + (int64_t)(wrapn(ty0 + r, Ky, kym)) * Kx + (wrapn(tx0 + c, Kx, kxm)));
         }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1)
             const R fx = __shfl_sync(0xffffffffu, pfx, src);
             const R fy = __shfl_sync(0xffffffffu, pfy, src);
             // window start relative to the staged region: 0..32 (carry included)
-            const int ox = (((cxv - 3) & (Kx - 1)) - tx0) & (Kx - 1);
-            const int oy = (((cyv - 3) & (Ky - 1)) - ty0) & (Ky - 1);
+            const int ox = wrapn(wrapn(cxv - 3, Kx, kxm) - tx0, Kx, kxm);
+            const int oy = wrapn(wrapn(cyv - 3, Ky, kym) - ty0, Ky, kym);
             off[h] = min(oy, DG_REG - 8) * DG_LDS + min(ox, DG_REG - 8) + j;
             pu[h] = horner<R, NC>(c, (R)2 * fx - (R)1);
             pv[h] = horner<R, NC>(c, (R)2 * fy - (R)1);
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
     const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
     const int ty0 = tyi * TY, tx0 = txi * TX;
     const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int kxm = a.g.kxm, kym = a.g.kym;
     for (int k = threadIdx.x; k < GRID_WARPS * cells; k += blockDim.x) {
         acc[k] = cx<R>(0, 0);
         if (KAHAN) cmp[k] = cx<R>(0, 0);
@@ -308,8 +310,8 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
         if (i >= 0) {
             int cxv, cyv;
             VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
-            const int k0x = (cxv - 3) & (Kx - 1);
-            const int k0y = (cyv - 3) & (Ky - 1);
+            const int k0x = wrapn(cxv - 3, Kx, kxm);
+            const int k0y = wrapn(cyv - 3, Ky, kym);
             CT val;
             if (MODE == GIN_CALLER) {
                 val = a.in[a.perm[i]];
@@ -335,14 +337,14 @@ __global__ void __launch_bounds__(GRID_WARPS * 32) k_grid(NufftK<R> a, const Gri
         for (int k = 0; k < nb; ++k) {
             const int2 b0 = s_k0[w][k];
             if (b0.x < 0) continue;
-            const int gx = ((b0.x + cc) & (Kx - 1)) - tx0;
+            const int gx = (wrapn(b0.x + cc, Kx, kxm)) - tx0;
             if (gx >= 0 && gx < TX) {
                 const CT vv = s_val[w][k];
                 const R pu = s_phi[w][k][cc];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int rr = r0 + 4 * q;
-                    const int gy = ((b0.y + rr) & (Ky - 1)) - ty0;
+                    const int gy = (wrapn(b0.y + rr, Ky, kym)) - ty0;
                     if (gy < 0 || gy >= TY) continue;
                     const R wgt = pu * s_phi[w][k][8 + rr];
                     const int cell = gy * TX + gx;
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
     const int tyi = t / a.g.ntx, txi = t - tyi * a.g.ntx;
     const int ty0 = tyi * TY, tx0 = txi * TX;
     const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int kxm = a.g.kxm, kym = a.g.kym;
     for (int k = threadIdx.x; k < GRID_PW * TCELLS; k += blockDim.x) priv[k] = cx<R>(0, 0);
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -453,8 +456,8 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
             if (i >= 0) {
                 int cxv, cyv;
                 VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
-                k0x = (cxv - 3) & (Kx - 1);
-                k0y = (cyv - 3) & (Ky - 1);
+                k0x = wrapn(cxv - 3, Kx, kxm);
+                k0y = wrapn(cyv - 3, Ky, kym);
                 if (MODE == GIN_CALLER) {
                     val = a.in[a.perm[i]];
                 } else if (MODE == GIN_SORTED) {
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
             if (sx < 0) continue;   // padding; uniform over the 8 lanes of a window
             const R phx = horner<R, NC>(c, (R)2 * sfx - (R)1);   // phi_u of column j
             const R phy = horner<R, NC>(c, (R)2 * sfy - (R)1);   // phi_v of row j
-            const int gx = ((sx + j) & (Kx - 1)) - tx0;
+            const int gx = (wrapn(sx + j, Kx, kxm)) - tx0;
             const bool colok = (unsigned)gx < (unsigned)TX;
             const R pr = phx * vr, pi = phx * vi;
             // the 8 rows of a window are distinct cells: load all, add, store all
@@ -487,7 +490,7 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
             bool ok[8];
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                const int gy = ((sy + r) & (Ky - 1)) - ty0;
+                const int gy = (wrapn(sy + r, Ky, kym)) - ty0;
                 ok[r] = colok && (unsigned)gy < (unsigned)TY;
                 off[r] = gy * GRID_LDT + gx;
                 if (ok[r]) cur[r] = mine[off[r]];
@@ -567,6 +570,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1)
     if (wi >= n_items) return;
     const SweepItem it = items[wi];
     const int Kx = a.g.Kx, Ky = a.g.Ky;
+    const int kxm = a.g.kxm, kym = a.g.kym;
     const int c0 = it.strip * GRID_TILE, row0 = it.row0, H = it.row1 - it.row0;
     CT* out = a.grid_out + (int64_t)it.l * Ky * Kx + (int64_t)row0 * Kx + c0 + lane;
     R* st = stage[w];
@@ -593,10 +597,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1)
             int cxv, cyv;
             R fx, fy;
             VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
-            const int k0x = (cxv - 3) & (Kx - 1);
-            const int k0y = (cyv - 3) & (Ky - 1);
-            rx = ((k0x - c0 + 7) & (Kx - 1)) - 7;     // -7 .. 31
-            ry = ((k0y - row0 + 7) & (Ky - 1)) - 7;   // -7 .. H - 1
+            const int k0x = wrapn(cxv - 3, Kx, kxm);
+            const int k0y = wrapn(cyv - 3, Ky, kym);
+            rx = (wrapn(k0x - c0 + 7, Kx, kxm)) - 7;     // -7 .. 31
+            ry = (wrapn(k0y - row0 + 7, Ky, kym)) - 7;   // -7 .. H - 1
             CT val;
             if (MODE == GIN_CALLER) {
                 val = a.in[a.perm[i]];

@@ -70,6 +70,19 @@ void plan_free(Plan* p) {
 }
 
 static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+// x mod K for any x (grids need not be powers of two).
+static inline int modk(int64_t x, int K) { return (int)(((x % K) + K) % K); }
+// Image sides the kernels support: r 2^a with r in {1, 3, 5} (FFT lines of
+// 2 r 2^a), at least 16, and multiples of 16 unless powers of two (gridding
+// tiles and strips of 32 cells).
+static bool side_ok(int n) {
+    if (n < 16 || n > 2048) return false;
+    if (pow2(n)) return true;
+    int m = n;
+    if (m % 5 == 0) m /= 5;
+    else if (m % 3 == 0) m /= 3;
+    return pow2(m) && n % 16 == 0;
+}
 static int ilog2(int v) {
     int r = 0;
     while ((1 << r) < v) ++r;
@@ -140,9 +153,9 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
         for (auto& v : strips) v.clear();
         for (int64_t r = off[l]; r < off[l + 1]; ++r) {
             const int k0x = k0xs[r], k0y = k0ys[r];
-            const int s0 = k0x / GRID_TILE, s1 = ((k0x + 7) & (Kx - 1)) / GRID_TILE;
+            const int s0 = k0x / GRID_TILE, s1 = modk(k0x + 7, Kx) / GRID_TILE;
             strips[s0].push_back({k0y, k0x - s0 * GRID_TILE, (int)r});
-            if (s1 != s0) strips[s1].push_back({k0y, ((k0x - s1 * GRID_TILE + 7) & (Kx - 1)) - 7, (int)r});
+            if (s1 != s0) strips[s1].push_back({k0y, modk(k0x - s1 * GRID_TILE + 7, Kx) - 7, (int)r});
         }
         for (int st = 0; st < nstrip; ++st) {
             std::vector<Win>& ws = strips[st];
@@ -157,7 +170,7 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
             for (const Win& w : ws) ++rowcnt[w.y];
             for (int row0 = 0; row0 < Ky;) {
                 int64_t cnt = 0;
-                for (int d = 1; d <= 7; ++d) cnt += rowcnt[(row0 - d) & (Ky - 1)];
+                for (int d = 1; d <= 7; ++d) cnt += rowcnt[modk(row0 - d, Ky)];
                 int row1 = row0;
                 while (row1 < Ky && row1 - row0 < hmax && (row1 == row0 || cnt + rowcnt[row1] <= cap))
                     cnt += rowcnt[row1++];
@@ -166,7 +179,7 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
                 seg.clear();
                 auto take = [&](int ya, int yb) {
                     for (auto it = row_at(ya); it != ws.end() && it->y < yb; ++it)
-                        seg.push_back({((it->y - row0 + 7) & (Ky - 1)) - 7, it->x, it->r});
+                        seg.push_back({modk(it->y - row0 + 7, Ky) - 7, it->x, it->r});
                 };
                 if (row0 >= 7) {
                     take(row0 - 7, row1);
@@ -215,8 +228,8 @@ static hs_status build_sweep(Plan* p, const std::vector<int>& perm, const std::v
     std::vector<int> k0x(M), k0y(M);
     for (int64_t r = 0; r < M; ++r) {
         const int64_t i = perm[r];
-        k0x[r] = (cellx[i] - 3) & (Kx - 1);
-        k0y[r] = (celly[i] - 3) & (Ky - 1);
+        k0x[r] = modk(cellx[i] - 3, Kx);
+        k0y[r] = modk(celly[i] - 3, Ky);
     }
     std::vector<SweepItem> items;
     std::vector<int> ent;
@@ -435,7 +448,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
         const int64_t a = p->blk_off_h[kb], b = p->blk_off_h[kb + 1];
         keys.resize(b - a);
         for (int64_t i = a; i < b; ++i) {
-            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+            const int k0x = modk(cellx[i] - 3, Kx), k0y = modk(celly[i] - 3, Ky);
             const uint64_t tile = (uint64_t)(k0y / TY) * g.ntx + (uint64_t)(k0x / TX);
             const uint64_t key = (tile * TY + (uint64_t)(k0y % TY)) * TX + (uint64_t)(k0x % TX);
             keys[i - a] = (key << 32) | (uint64_t)(i - a);
@@ -465,7 +478,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
             while (r < b) {
                 auto tile_of = [&](int64_t rr) {
                     const int64_t i = perm[rr];
-                    const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+                    const int k0x = modk(cellx[i] - 3, Kx), k0y = modk(celly[i] - 3, Ky);
                     return (int64_t)(k0y / TY) * g.ntx + k0x / TX;
                 };
                 const int64_t t = tile_of(r);
@@ -500,11 +513,11 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
             uint64_t qy = (uint64_t)std::llround(std::ldexp(fy[i], g.fby));
             if (qx >= (1ull << g.fbx)) {
                 qx = 0;
-                cxv = (cxv + 1) & (Kx - 1);
+                cxv = modk(cxv + 1, Kx);
             }
             if (qy >= (1ull << g.fby)) {
                 qy = 0;
-                cyv = (cyv + 1) & (Ky - 1);
+                cyv = modk(cyv + 1, Ky);
             }
             c[2 * r] = ((uint32_t)cxv << g.fbx) | (uint32_t)qx;
             c[2 * r + 1] = ((uint32_t)cyv << g.fby) | (uint32_t)qy;
@@ -546,11 +559,11 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
         std::vector<int64_t> toff((size_t)L * nt + 1, 0);
         auto tiles_of = [&](int64_t r, int* txs, int* tys, int& ntx_, int& nty_) {
             const int64_t i = perm[r];
-            const int k0x = (cellx[i] - 3) & (Kx - 1), k0y = (celly[i] - 3) & (Ky - 1);
+            const int k0x = modk(cellx[i] - 3, Kx), k0y = modk(celly[i] - 3, Ky);
             txs[0] = k0x / TX;
-            txs[1] = ((k0x + 7) & (Kx - 1)) / TX;
+            txs[1] = modk(k0x + 7, Kx) / TX;
             tys[0] = k0y / TY;
-            tys[1] = ((k0y + 7) & (Ky - 1)) / TY;
+            tys[1] = modk(k0y + 7, Ky) / TY;
             ntx_ = txs[1] != txs[0] ? 2 : 1;
             nty_ = tys[1] != tys[0] ? 2 : 1;
         };
@@ -602,7 +615,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
                 for (int64_t q = toff[tix]; q < toff[tix + 1]; ++q) {
                     const int r = ent[q];
                     const int64_t i = perm[r];
-                    const int x = (cellx[i] - 3) & (Kx - 1), y = (celly[i] - 3) & (Ky - 1);
+                    const int x = modk(cellx[i] - 3, Kx), y = modk(celly[i] - 3, Ky);
                     bool placed = false;
                     for (size_t gi = 0; gi < open.size() && !placed; ++gi) {
                         Group& g = open[gi];
@@ -732,14 +745,21 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
     if (out == nullptr) return fail(HS_ERR_ARG, "out is null");
     *out = nullptr;
     if (vis_offsets == nullptr) return fail(HS_ERR_ARG, "vis_offsets is null");
-    if (!pow2(nx) || !pow2(ny) || nx < 16 || ny < 16 || nx > 2048 || ny > 2048)
-        return fail(HS_ERR_ARG, "nx, ny must be powers of two in [16, 2048] (got %d x %d)", nx, ny);
+    if (!side_ok(nx) || !side_ok(ny))
+        return fail(HS_ERR_ARG, "nx, ny must be in [16, 2048] and powers of two, or 3 or 5 times a power of two "
+                                "and multiples of 16 (got %d x %d)", nx, ny);
     if (L < 1 || L > 1024) return fail(HS_ERR_ARG, "L must be in [1, 1024] (got %d)", L);
     if (oversample != 2) return fail(HS_ERR_ARG, "oversample must be 2 (got %d)", oversample);
     if (J != 8) return fail(HS_ERR_ARG, "J must be 8 (got %d)", J);
     if (levels < 1 || levels > 8 || (nx >> levels) < 1 || (ny >> levels) < 1 ||
         nx % (1 << levels) || ny % (1 << levels))
         return fail(HS_ERR_ARG, "wavelet_levels %d incompatible with %d x %d", levels, nx, ny);
+    for (int lev = 0; lev < levels; ++lev) {   // DWT tiles: 16 coefficients per subband side, or one tile
+        const int hy = ny >> (lev + 1), hx = nx >> (lev + 1);
+        if ((hy >= 16 && hy % 16) || (hx >= 16 && hx % 16))
+            return fail(HS_ERR_ARG, "wavelet_levels %d: level %d subbands of %d x %d are not multiples of 16",
+                        levels, lev, hy, hx);
+    }
     if (prec != HS_F32 && prec != HS_F64) return fail(HS_ERR_ARG, "bad precision %d", (int)prec);
     if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA | HS_PLAN_NO_TUNE))
         return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
@@ -765,6 +785,8 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
     g.Ky = oversample * ny;
     g.fbx = std::min(23, 32 - ilog2(g.Kx));
     g.fby = std::min(23, 32 - ilog2(g.Ky));
+    g.kxm = pow2(g.Kx) ? g.Kx - 1 : -1;
+    g.kym = pow2(g.Ky) ? g.Ky - 1 : -1;
     g.tx = std::min(GRID_TILE, g.Kx);
     g.ty = std::min(GRID_TILE, g.Ky);
     g.ntx = g.Kx / g.tx;

@@ -37,7 +37,7 @@ CANDIDATES = [(0, 0), (32, 512), (128, 2048)]
 
 
 @pytest.mark.parametrize("hmax_req,cap", CANDIDATES)
-@pytest.mark.parametrize("Kx,Ky", [(64, 64), (128, 64), (64, 256)])
+@pytest.mark.parametrize("Kx,Ky", [(64, 64), (128, 64), (64, 256), (160, 96)])
 def test_lists_meet_the_kernel_conditions(Kx, Ky, hmax_req, cap):
     off, k0x, k0y, _ = _windows(3, Kx, Ky, 3, (1500, 0, 900))
     items, ent = hs.sweep_lists(Kx, Ky, off, k0x, k0y, hmax_req, cap)
@@ -131,7 +131,7 @@ def test_sweep_on_the_lists_equals_direct_gridding(hmax_req, cap):
 def test_bad_arguments_are_rejected():
     off = np.array([0, 2], dtype=np.int64)
     with pytest.raises(hs.HSError):
-        hs.sweep_lists(96, 64, off, [0, 1], [0, 1])    # not a power of two
+        hs.sweep_lists(80, 64, off, [0, 1], [0, 1])    # columns not a multiple of the 32-column strip
     with pytest.raises(hs.HSError):
         hs.sweep_lists(32, 64, off, [0, 1], [0, 1])    # narrower than two strips
     with pytest.raises(hs.HSError):
