@@ -168,6 +168,16 @@ typedef struct {
 HS_API hs_status hs_plan_info(hs_plan_t plan, hs_plan_info_t* info);
 
 /*
+ * hs_set_device_limit - cap the device memory the library's plans and PD
+ * states may hold in this process, in bytes (0: no cap, the default). An
+ * allocation that would pass it fails with HS_ERR_NOMEM before cudaMalloc is
+ * called, and the plan or state being created is released. Existing
+ * allocations are not affected. hs_device_bytes reports what is held now.
+ */
+HS_API hs_status hs_set_device_limit(int64_t bytes);
+HS_API hs_status hs_device_bytes(int64_t* out);
+
+/*
  * hs_plan_check - synchronise the stream and report whether a kernel of this
  * plan (or of a PD state on it) failed on the device since the last check
  * (the flag is then cleared): HS_ERR_TIMEOUT if a bounded device-side wait
@@ -307,6 +317,19 @@ HS_API hs_status hs_proj_l2ball_static(int L, const int64_t* vis_offsets, const 
  */
 HS_API hs_status hs_norm_l21(hs_plan_t plan, const void* A, const void* w_rows, double* out_host,
                       void* stream);
+
+/*
+ * hs_estimate_mu - the regularisation parameter mu = ||X_d||_* / ||Psi^dagger X_d||_{2,1}
+ * of the dirty cube X_d,l = eta_l Phi_l^dagger y_l (Sec. 2.3), with the PSF
+ * normalisation eta_l = 1 / max(Phi_l^dagger Phi_l delta), delta the unit image
+ * at the phase centre (Sec. 4.3). Y: DEVICE total complex (caller order);
+ * A_work: DEVICE 9 x L x ny x nx reals of scratch (the caller's); eta_out:
+ * DEVICE L doubles or NULL; Xd_out: DEVICE L x ny x nx reals or NULL (the
+ * dirty cube). The nuclear norm comes from the Gram route of hs_prox_nuclear
+ * (L <= 64). Synchronises the stream; *mu_host is valid on return.
+ */
+HS_API hs_status hs_estimate_mu(hs_plan_t plan, const void* Y, void* A_work, double* eta_out, void* Xd_out,
+                                double* mu_host, void* stream);
 
 /*
  * hs_op_norm2 - max_l ||U_l^{1/2} Phi_l||_S^2 by power iteration on

@@ -61,6 +61,7 @@ struct hs_pd_state {
     cudaGraphExec_t gexec = nullptr;
     void* ystage = nullptr;   // caller-order y staged from host memory (hs_pd_set_data_host)
     std::vector<void*> allocs;
+    std::vector<size_t> alloc_bytes;
 };
 
 static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -214,6 +215,20 @@ static hs_status take_device_error(Plan* p, cudaStream_t s) {
     HS_CHECK_CUDA(cudaStreamSynchronize(s));
     if (err & 1) return fail(HS_ERR_TIMEOUT, "a bounded device-side wait expired (tensor-core Gram)");
     return fail(HS_ERR_ARG, "an input magnitude reached 2^60, beyond the tensor-core Gram's range");
+}
+
+hs_status hs_set_device_limit(int64_t bytes) {
+    clear_error();
+    if (bytes < 0) return fail(HS_ERR_ARG, "hs_set_device_limit: bytes must be >= 0");
+    set_device_limit(bytes);
+    return HS_OK;
+}
+
+hs_status hs_device_bytes(int64_t* out) {
+    clear_error();
+    if (out == nullptr) return fail(HS_ERR_ARG, "hs_device_bytes: out is null");
+    *out = device_bytes_held();
+    return HS_OK;
 }
 
 hs_status hs_plan_check(hs_plan_t plan, void* stream) {
@@ -399,6 +414,43 @@ static uint64_t splitmix64(uint64_t& x) {
     return z ^ (z >> 31);
 }
 
+hs_status hs_estimate_mu(hs_plan_t plan, const void* Y, void* A_work, double* eta_out, void* Xd_out,
+                         double* mu_host, void* stream) {
+    clear_error();
+    CHECK_PLAN(plan);
+    Plan* p = plan->p;
+    if (A_work == nullptr || mu_host == nullptr || (Y == nullptr && p->M_total > 0))
+        return fail(HS_ERR_ARG, "hs_estimate_mu: null argument");
+    const int L = p->g.L;
+    if (L > MAX_L_NUC) return fail(HS_ERR_ARG, "hs_estimate_mu: L = %d exceeds %d", L, MAX_L_NUC);
+    cudaStream_t s = S(stream);
+    double* eta = eta_out ? eta_out : p->dscal + 2 * L;
+    HS_TRY(psf_inv_peak(p, p->xbuf, eta, s));
+    void* Xd = Xd_out ? Xd_out : p->xbuf2;
+    if (p->M_total > 0) {   // dirty cube eta_l Phi_l^dagger y_l
+        GridArgs ga{};
+        ga.mode = GIN_CALLER;
+        ga.in = Y;
+        HS_TRY(grid(p, ga, s));
+        HS_TRY(fft_adjoint(p, Xd, s));
+    } else {
+        HS_CHECK_CUDA(cudaMemsetAsync(Xd, 0, (size_t)L * p->N() * p->rsize(), s));
+    }
+    HS_TRY(mul_channels(p, Xd, eta, s));
+    HS_TRY(nuclear_svals(p, Xd, p->sv, s));
+    HS_TRY(dwt_analysis(p, Xd, A_work, s));
+    HS_TRY(l21_norm(p, A_work, nullptr, p->dscal, s));
+    std::vector<double> sv(L);
+    double l21 = 0.0;
+    HS_CHECK_CUDA(cudaMemcpyAsync(sv.data(), p->sv, L * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HS_CHECK_CUDA(cudaMemcpyAsync(&l21, p->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HS_TRY(take_device_error(p, s));
+    double nuc = 0.0;
+    for (int l = 0; l < L; ++l) nuc += sv[l];
+    *mu_host = l21 > 0.0 ? nuc / l21 : 0.0;
+    return HS_OK;
+}
+
 hs_status hs_op_norm2(hs_plan_t plan, int iters, double tol, uint64_t seed, double* out_host,
                       void* stream) {
     clear_error();
@@ -466,13 +518,9 @@ hs_status hs_op_norm2(hs_plan_t plan, int iters, double tol, uint64_t seed, doub
 static hs_status st_alloc(hs_pd_state* st, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(ptr, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *ptr = nullptr;
-        return fail(HS_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
+    HS_TRY(lib_alloc(ptr, bytes));
     st->allocs.push_back(*ptr);
+    st->alloc_bytes.push_back(bytes);
     return HS_OK;
 }
 
@@ -485,8 +533,9 @@ static void st_free(hs_pd_state* st) {
     if (st->side) cudaStreamDestroy(st->side);
     if (st->side2) cudaStreamDestroy(st->side2);
     if (st->cap) cudaStreamDestroy(st->cap);
-    for (void* q : st->allocs) cudaFree(q);
+    for (size_t k = 0; k < st->allocs.size(); ++k) lib_free(st->allocs[k], st->alloc_bytes[k]);
     st->allocs.clear();
+    st->alloc_bytes.clear();
 }
 
 __global__ void k_gather_c2(const float2* __restrict__ in, const int* __restrict__ perm,

@@ -159,6 +159,12 @@ struct Plan {
 
 // Device allocation tracked by the plan (freed in destroy).
 hs_status plan_alloc(Plan* p, void** ptr, size_t bytes);
+// Every device allocation of the library goes through these (process-wide
+// accounting and the optional limit of hs_set_device_limit).
+hs_status lib_alloc(void** ptr, size_t bytes);
+void lib_free(void* ptr, size_t bytes);
+void set_device_limit(int64_t bytes);
+int64_t device_bytes_held();
 
 // ---------------------------------------------------------------- host tables
 hs_status daubechies_lowpass(int p, double* out);
@@ -263,6 +269,10 @@ hs_status primal_update(Plan* p, int64_t n, const void* P, const void* At, const
                         void* X, void* Xt, double* part, int nparts, cudaStream_t s);
 hs_status beta_from_partials(const double* part, int nparts, double* beta, int64_t* t_count, cudaStream_t s);
 hs_status channel_norms(Plan* p, const void* X, double* out_dev, cudaStream_t s);
+// eta_l = 1 / max(Phi_l^dagger Phi_l delta) into eta (device L); X: L x N scratch.
+hs_status psf_inv_peak(Plan* p, void* X, double* eta, cudaStream_t s);
+// X[l] *= f[l] (device L doubles).
+hs_status mul_channels(Plan* p, void* X, const double* f, cudaStream_t s);
 hs_status scale_channels(Plan* p, void* X, const double* norms, cudaStream_t s);
 
 }  // namespace hs

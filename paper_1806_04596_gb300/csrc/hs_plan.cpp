@@ -16,6 +16,7 @@
 //  * the Kaiser-Bessel polynomial pieces, the Z scaling, the FFT twiddles;
 //  * all scratch buffers, so that no compute call allocates.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <functional>
@@ -36,15 +37,44 @@ hs_status prox_init();
 hs_status eig_init();
 int64_t gram_part_doubles(int L);
 
-hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
+// Device memory held by the library's plans and PD states (process-wide), and
+// the optional cap on it (hs_set_device_limit; 0: none).
+static std::atomic<int64_t> g_lib_bytes{0};
+static std::atomic<int64_t> g_lib_limit{0};
+
+void set_device_limit(int64_t bytes) { g_lib_limit.store(bytes < 0 ? 0 : bytes); }
+int64_t device_bytes_held() { return g_lib_bytes.load(); }
+
+hs_status lib_alloc(void** ptr, size_t bytes) {
     *ptr = nullptr;
-    if (bytes == 0) return HS_OK;
+    const int64_t lim = g_lib_limit.load();
+    const int64_t now = g_lib_bytes.fetch_add((int64_t)bytes) + (int64_t)bytes;
+    if (lim > 0 && now > lim) {
+        g_lib_bytes.fetch_sub((int64_t)bytes);
+        return fail(HS_ERR_NOMEM, "allocation of %zu bytes would pass the library's device limit (%lld of %lld held)",
+                    bytes, (long long)(now - (int64_t)bytes), (long long)lim);
+    }
     cudaError_t e = cudaMalloc(ptr, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
+        g_lib_bytes.fetch_sub((int64_t)bytes);
         return fail(HS_ERR_NOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
     }
+    return HS_OK;
+}
+
+void lib_free(void* ptr, size_t bytes) {
+    if (ptr) {
+        cudaFree(ptr);
+        g_lib_bytes.fetch_sub((int64_t)bytes);
+    }
+}
+
+hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return HS_OK;
+    HS_TRY(lib_alloc(ptr, bytes));
     p->allocs.push_back(*ptr);
     p->alloc_bytes.push_back(bytes);
     p->device_bytes += (int64_t)bytes;
@@ -55,7 +85,7 @@ hs_status plan_alloc(Plan* p, void** ptr, size_t bytes) {
 static void plan_release(Plan* p, void* ptr) {
     for (size_t k = 0; k < p->allocs.size(); ++k)
         if (p->allocs[k] == ptr) {
-            cudaFree(ptr);
+            lib_free(ptr, p->alloc_bytes[k]);
             p->device_bytes -= (int64_t)p->alloc_bytes[k];
             p->allocs.erase(p->allocs.begin() + k);
             p->alloc_bytes.erase(p->alloc_bytes.begin() + k);
@@ -64,7 +94,7 @@ static void plan_release(Plan* p, void* ptr) {
 }
 
 void plan_free(Plan* p) {
-    for (void* q : p->allocs) cudaFree(q);
+    for (size_t k = 0; k < p->allocs.size(); ++k) lib_free(p->allocs[k], p->alloc_bytes[k]);
     p->allocs.clear();
     p->alloc_bytes.clear();
 }

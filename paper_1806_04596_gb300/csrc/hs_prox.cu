@@ -802,4 +802,71 @@ hs_status scale_channels(Plan* p, void* X, const double* norms, cudaStream_t s) 
     return HS_OK;
 }
 
+// out[l] = 1 / max_n X[l][n] (0 when the maximum is not positive): the PSF
+// normalisation eta_l of the dirty cube.
+template <typename R>
+__global__ void k_channel_inv_max(const R* __restrict__ X, int64_t N, double* __restrict__ out) {
+    __shared__ double red[32];
+    const int l = blockIdx.x;
+    double m = -1e300;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, (double)X[(int64_t)l * N + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, red[w]);
+        out[l] = b > 0.0 ? 1.0 / b : 0.0;
+    }
+}
+
+// X[l][n] *= f[l]
+template <typename R>
+__global__ void k_channel_mul(R* __restrict__ X, int64_t N, const double* __restrict__ f) {
+    const int l = blockIdx.y;
+    const R v = (R)f[l];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        X[(int64_t)l * N + i] *= v;
+}
+
+// The unit image at the phase centre (pixel (ny / 2, nx / 2)) in every channel.
+template <typename R> __global__ void k_set_delta(R* __restrict__ X, int64_t N, int64_t centre) {
+    X[(int64_t)blockIdx.x * N + centre] = (R)1;
+}
+
+hs_status psf_inv_peak(Plan* p, void* X, double* eta, cudaStream_t s) {
+    const int L = p->g.L;
+    const int64_t N = p->N(), centre = (int64_t)(p->g.ny / 2) * p->g.nx + p->g.nx / 2;
+    HS_CHECK_CUDA(cudaMemsetAsync(X, 0, (size_t)L * N * p->rsize(), s));
+    if (p->prec == HS_F32) k_set_delta<float><<<L, 1, 0, s>>>((float*)X, N, centre);
+    else k_set_delta<double><<<L, 1, 0, s>>>((double*)X, N, centre);
+    HS_CHECK_LAUNCH();
+    if (p->M_total > 0) {
+        HS_TRY(fft_forward(p, X, s));
+        DegridArgs da{};
+        da.mode = DOUT_SORTED;
+        da.out = p->vis;
+        HS_TRY(degrid(p, da, s));
+        GridArgs ga{};
+        ga.mode = GIN_SORTED;
+        ga.in = p->vis;
+        HS_TRY(grid(p, ga, s));
+        HS_TRY(fft_adjoint(p, X, s));
+    } else {
+        HS_CHECK_CUDA(cudaMemsetAsync(X, 0, (size_t)L * N * p->rsize(), s));
+    }
+    if (p->prec == HS_F32) k_channel_inv_max<float><<<L, 256, 0, s>>>((const float*)X, N, eta);
+    else k_channel_inv_max<double><<<L, 256, 0, s>>>((const double*)X, N, eta);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
+hs_status mul_channels(Plan* p, void* X, const double* f, cudaStream_t s) {
+    dim3 g(64, p->g.L);
+    if (p->prec == HS_F32) k_channel_mul<float><<<g, 256, 0, s>>>((float*)X, p->N(), f);
+    else k_channel_mul<double><<<g, 256, 0, s>>>((double*)X, p->N(), f);
+    HS_CHECK_LAUNCH();
+    return HS_OK;
+}
+
 }  // namespace hs

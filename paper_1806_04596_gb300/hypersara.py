@@ -73,6 +73,8 @@ _SIGS = {
     "hs_plan_destroy": ([_P], C.c_int),
     "hs_plan_info": ([_P, C.POINTER(PlanInfo)], C.c_int),
     "hs_plan_check": ([_P, _P], C.c_int),
+    "hs_set_device_limit": ([C.c_int64], C.c_int),
+    "hs_device_bytes": ([C.POINTER(C.c_int64)], C.c_int),
     "hs_phi_fwd": ([_P, _P, _P, _P], C.c_int),
     "hs_phi_adj": ([_P, _P, _P, _P], C.c_int),
     "hs_psi_fwd": ([_P, _P, _P, _P], C.c_int),
@@ -85,6 +87,7 @@ _SIGS = {
     "hs_proj_l2ball_static": ([C.c_int, _P, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P], C.c_int),
     "hs_norm_l21": ([_P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
     "hs_op_norm2": ([_P, C.c_int, C.c_double, C.c_uint64, C.POINTER(C.c_double), _P], C.c_int),
+    "hs_estimate_mu": ([_P, _P, _P, _P, _P, C.POINTER(C.c_double), _P], C.c_int),
     "hs_pd_state_create": ([_P, _P, _P, C.POINTER(PDParams), C.POINTER(C.c_void_p), _P], C.c_int),
     "hs_pd_state_destroy": ([_P], C.c_int),
     "hs_pd_set_data": ([_P, _P, _P, _P], C.c_int),
@@ -137,6 +140,18 @@ def version() -> str:
 def last_error() -> str:
     """The calling thread's last error message (hs_last_error)."""
     return load().hs_last_error().decode(errors="replace")
+
+
+def set_device_limit(nbytes: int):
+    """hs_set_device_limit: cap on the device memory plans and states hold (0: none)."""
+    _check("hs_set_device_limit", load().hs_set_device_limit(int(nbytes)))
+
+
+def device_bytes() -> int:
+    """hs_device_bytes: device memory the library's plans and states hold now."""
+    v = C.c_int64()
+    _check("hs_device_bytes", load().hs_device_bytes(C.byref(v)))
+    return v.value
 
 
 def daubechies_lowpass(p: int) -> np.ndarray:
@@ -413,6 +428,17 @@ class Plan:
         _check("hs_time_stage", load().hs_time_stage(self.h, STAGES[stage], _ptr(inp), _ptr(out), int(reps),
                                                      C.byref(ms), _stream()))
         return ms.value
+
+    def estimate_mu(self, Y, A_work=None):
+        """hs_estimate_mu: (mu, eta per channel as an FP64 CUDA tensor, dirty cube)."""
+        torch = _torch()
+        A_work = self.cube(9) if A_work is None else A_work
+        pY, pA = _args(self._vis(Y, "Y"), self._img(A_work, "A_work", 9))
+        eta = torch.empty(self.L, dtype=torch.float64, device="cuda")
+        Xd = self.cube()
+        mu = C.c_double()
+        _check("hs_estimate_mu", load().hs_estimate_mu(self.h, pY, pA, _ptr(eta), _ptr(Xd), C.byref(mu), _stream()))
+        return mu.value, eta, Xd
 
     def op_norm2(self, iters: int = 500, tol: float = 1e-10, seed: int = 0) -> float:
         r = C.c_double()

@@ -8,8 +8,10 @@ GPU:
   X_dirty,l = eta_l Phi_l^dagger y_l,  eta_l = 1 / max(Phi_l^dagger Phi_l delta),
   mu = ||X_dirty||_* / ||Psi^dagger X_dirty||_{2,1}                (Sec. 2.3),
   kappa_3 = 1 / max_l ||U_l^{1/2} Phi_l||^2 by power iteration    (Sec. 3.4).
-Scalar bookkeeping (norms of a few vectors, the maximum of a PSF) uses torch
-reductions on the device; every operator application is a library call.
+mu (the dirty cube's PSF normalisation, nuclear and l2,1 norms) comes from
+hs_estimate_mu; the noise level sigma is the norm of the clean visibilities (a
+torch reduction: part of synthesising the data); every operator application is
+a library call.
 """
 
 from __future__ import annotations
@@ -48,19 +50,8 @@ def build(inp, prec: str = "f32", levels: int = 4, compensated: bool = False,
     y = y + (sigma * torch.tensor(inp.noise, dtype=torch.complex128, device="cuda")).to(cdt)
     Ml = np.diff(inp.offsets).astype(np.float64)
     eps = torch.tensor(sigma * np.sqrt(Ml + 2.0 * np.sqrt(Ml)), dtype=torch.float64, device="cuda")
-    # dirty cube and mu
-    delta = torch.zeros((plan.L, plan.ny, plan.nx), dtype=rdt, device="cuda")
-    delta[:, plan.ny // 2, plan.nx // 2] = 1.0
-    psf = plan.phi_adj(plan.phi_fwd(delta))
-    peak = psf.reshape(plan.L, -1).amax(dim=1).to(torch.float64)
-    eta = torch.where(peak > 0, 1.0 / peak, torch.zeros_like(peak))
-    Xd = (plan.phi_adj(y).to(torch.float64) * eta[:, None, None]).to(rdt)
-    nuc = 0.0
-    if plan.L <= 64:
-        _, sv = plan.prox_nuclear(Xd, 0.0)
-        nuc = float(sv.sum())
-    l21 = plan.norm_l21(plan.psi_fwd(Xd))
-    mu = nuc / l21 if l21 > 0 else 0.0
+    # mu from the dirty cube (PSF normalisation, nuclear and l2,1 norms: hs_estimate_mu)
+    mu = plan.estimate_mu(y)[0] if plan.L <= 64 else 0.0
     on2 = plan.op_norm2(iters=power_iters, tol=power_tol, seed=0)
     torch.cuda.synchronize()
     return DeviceProblem(plan=plan, truth=X, y=y, eps=eps, sigma=sigma, mu=mu,
