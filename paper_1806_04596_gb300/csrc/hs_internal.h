@@ -38,6 +38,7 @@ constexpr int NW = 8;                // wavelet bases
 constexpr int MAXF = 16;             // longest filter (db8)
 constexpr int KB_TERMS_F32 = 9;      // polynomial coefficients per unit piece, FP32
 constexpr int KB_TERMS_F64 = 14;     // ... FP64
+constexpr int KB_HALF = 7;           // even (or odd) coefficients of a piece, at most
 constexpr int GRID_TILE = 32;        // gridding tile side (cells)
 constexpr int GRID_WARPS = 4;        // warps per gridding CTA (private accumulators)
 constexpr int GRID_CAP = 512;        // most list entries one gridding CTA processes
@@ -117,6 +118,7 @@ struct Plan {
     int* sw_ent = nullptr;             // sweep lists: groups of 4 sorted visibility indices, -1 = padding
     int64_t n_sw_ent = 0;
     void* kbc = nullptr;               // 8 * kb_terms reals
+    std::vector<double> kbc_h;         // the same on the host
     void* cxs = nullptr;               // nx reals (Z scale along x)
     void* cys = nullptr;               // ny reals
     void* twx = nullptr;               // Kx complex, exp(-2 pi i m / Kx)

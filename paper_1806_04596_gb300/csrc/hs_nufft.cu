@@ -59,6 +59,10 @@ template <typename R> struct NufftK {
     const R* u;        // U (sorted) or null
     const int* perm;   // sorted -> caller
     const R* kbc;      // 8 x NC coefficients
+    // pieces 7 - m, m = 0 .. 3, split into even and odd coefficients (passed by value,
+    // so a warp-uniform Horner step reads its coefficient from the parameter bank)
+    R kev[4 * KB_HALF];
+    R kod[4 * KB_HALF];
     // de-gridding outputs / PD inputs
     Cx<R>* out;
     Cx<R>* v;
@@ -529,20 +533,25 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
 
 // Sweep gridding (grids of at least 64 x 64 cells, default kernel). A warp owns
 // one work item of the plan: a 32-column strip of one channel's grid and its
-// output rows [row0, row1). Lane c holds column c of two 8-row bands in
-// registers, A = rows 8j .. 8j + 7 and B = rows 8j + 8 .. 8j + 15 (relative to
-// row0), and walks the item's groups band by band: when a group of a later
-// band arrives, A is final, so it is stored (each output cell once, coalesced
-// 256-byte rows) and the bands move up (A = B, B = 0). A group holds up to 4
-// windows with disjoint columns starting in band j, so they all lie in A and B
-// and one pass over the 16 rows (2 x 16 FMAs per lane) adds them; no
-// shared-memory read-modify-write, no atomics, and a fixed summation order.
-// Lists are consumed in batches of 32 slots: lane q decodes slot q (coordinates,
-// weighted value, the 16 kernel taps) into shared memory, the row taps placed
-// at their rows of the 16-row window A, B (zeros elsewhere).
+// output rows [row0, row1). Lane c holds column c of two 8-row register banks P
+// and Q; band j (rows 8j .. 8j + 7 relative to row0) lives in P for even j and
+// in Q for odd j. The warp walks the item's groups band by band: a group holds
+// up to 4 windows with disjoint columns starting in band j, so they lie in
+// bands j and j + 1 and one pass over the 16 rows (2 x 16 FMAs per lane) adds
+// them; once a group of a later band arrives, band j is final, so its bank is
+// stored (each output cell once, coalesced 256-byte rows) and cleared for band
+// j + 2. The banks never move between registers, there is no shared-memory
+// read-modify-write, no atomics, and the summation order is fixed.
+// Lists are consumed in batches of 32 slots (8 groups): lane q decodes slot q
+// (window position, weighted value, the 16 kernel taps) into shared memory: the
+// 8 row taps at their rows of the 16-row window (zeros elsewhere), and for
+// every strip column the window covers, the column tap times the value and the
+// slot's place in its group, tagged with the batch number (a column whose entry
+// carries an older tag has no window in the group and adds zero, so the table
+// is never cleared), and the group pass reads one 16-byte entry per lane. The
+// next batch's list entries and inputs are loaded before the current batch's
+// groups are added.
 constexpr int SW_WARPS = 4;      // warps (work items) per CTA
-constexpr int SW_LD = 28;        // staged reals per slot: 8 column taps, 16 row taps, value, pad
-constexpr int SW_PAD = 1 << 20;  // start column of a padding slot (covers no lane)
 
 // 4 consecutive reals from 16-byte aligned shared memory
 __device__ __forceinline__ void sw_ld4(const float* p, float* v) {
@@ -554,17 +563,34 @@ __device__ __forceinline__ void sw_ld4(const double* p, double* v) {
     v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
 }
 
+// Column entry of a group: column tap x value of the window covering the
+// column and, in `slot`, 4 x the batch number + that window's slot in the group.
+template <typename R> struct __align__(16) SwCol {
+    R pr, pi;
+    int slot, pad;
+};
+
+// Inputs of one list slot loaded ahead of its decoding.
+template <typename R> struct SwRaw {
+    typename CxT<R>::T v;   // value (GIN_SORTED), d (GIN_PD)
+    R u, w;                 // U and Theta of the visibility (1 when absent)
+    int p;                  // caller index (GIN_CALLER) or data block (GIN_PD with blocks)
+};
+
 template <typename R, int NC, int MODE>
-__global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1)
-    k_grid_sweep(NufftK<R> a, const SweepItem* __restrict__ items,
+__global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
+    k_grid_sweep(const NufftK<R> a, const SweepItem* __restrict__ items,
                  const int* __restrict__ ent, int n_items) {
     typedef Cx<R> CT;
-    __shared__ __align__(16) R stage[SW_WARPS][32 * SW_LD];
-    __shared__ __align__(16) int sxs[SW_WARPS][32];   // start column of every slot (relative to the strip)
-    __shared__ int sjb[SW_WARPS][8];                  // band of every group
-    __shared__ R skb[8 * NC];
-    for (int k = threadIdx.x; k < 8 * NC; k += blockDim.x) skb[k] = a.kbc[k];
-    __syncthreads();
+    constexpr int NE = (NC + 1) / 2, NO = NC / 2;   // even / odd coefficients of a piece
+    // row taps of every slot, placed at their rows; the row stride (20 floats, 18
+    // doubles) puts the 4 slots of a group in disjoint banks for 16-byte loads
+    constexpr int RLD = sizeof(R) == 4 ? 20 : 18;
+    __shared__ __align__(16) R rowt[SW_WARPS][32][RLD];
+    // per group and strip column (rows padded to 33 entries: the decode's scattered
+    // 16-byte stores of different groups fall in different banks)
+    __shared__ __align__(16) SwCol<R> colt[SW_WARPS][8][33];
+    __shared__ int sjb[SW_WARPS][8];                          // band of every group
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wi = blockIdx.x * SW_WARPS + w;
     if (wi >= n_items) return;
@@ -573,94 +599,145 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 6 : 1)
     const int kxm = a.g.kxm, kym = a.g.kym;
     const int c0 = it.strip * GRID_TILE, row0 = it.row0, H = it.row1 - it.row0;
     CT* out = a.grid_out + (int64_t)it.l * Ky * Kx + (int64_t)row0 * Kx + c0 + lane;
-    R* st = stage[w];
-    CT A[8], B[8];
+    CT P[8], Q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) A[k] = B[k] = cx<R>(0, 0);
-    int jb = -1;   // band held in A (rows -8 .. -1 are never stored)
-    // store band A (rows 8 jb .. 8 jb + 7 inside [0, H)), move B into A
-    auto advance = [&]() {
+    for (int k = 0; k < 8; ++k) P[k] = Q[k] = cx<R>(0, 0);
+    int jb = -1;   // band whose rows are final next (rows -8 .. -1 are never stored)
+
+    // ---- loads of one slot's inputs (list entry i, -1 = padding)
+    auto load_raw = [&](int i, SwRaw<R>& r) {
+        r.u = r.w = (R)1;
+        r.p = 0;
+        if (i < 0) return;
+        if (MODE == GIN_CALLER) {
+            r.p = a.perm[i];
+        } else if (MODE == GIN_SORTED) {
+            r.v = reinterpret_cast<const typename CxT<R>::T*>(a.in)[i];
+        } else {
+            r.v = reinterpret_cast<const typename CxT<R>::T*>(a.d)[i];
+            if (a.blk) r.p = a.blk[i];
+            if (a.u) r.u = a.u[i];
+        }
+        if (a.w) r.w = a.w[i];
+    };
+    // ---- kernel taps of one axis: tap m is piece 7 - m of the window at s; pieces
+    // 7 - m and m are mirror images (phi is even), so taps m and 7 - m are
+    // E(s^2) + s O(s^2) and E(s^2) - s O(s^2) of piece 7 - m
+    auto taps = [&](R s, R* t) {
+        const R s2 = s * s;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            R e = a.kev[m * KB_HALF + NE - 1];
+#pragma unroll
+            for (int k = NE - 2; k >= 0; --k) e = fma(e, s2, a.kev[m * KB_HALF + k]);
+            R o = a.kod[m * KB_HALF + NO - 1];
+#pragma unroll
+            for (int k = NO - 2; k >= 0; --k) o = fma(o, s2, a.kod[m * KB_HALF + k]);
+            t[m] = fma(s, o, e);
+            t[7 - m] = fma(-s, o, e);
+        }
+    };
+    // ---- store the final band jb (rows 8 jb .. 8 jb + 7 inside [0, H)) and clear its bank
+    auto flush = [&](CT(&U)[8]) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int r = 8 * jb + k;
-            if ((unsigned)r < (unsigned)H) out[(int64_t)r * Kx] = A[k];
-            A[k] = B[k];
-            B[k] = cx<R>(0, 0);
+            if ((unsigned)r < (unsigned)H) out[(int64_t)r * Kx] = U[k];
+            U[k] = cx<R>(0, 0);
         }
+    };
+    auto advance = [&]() {
+        if (jb & 1) flush(Q);
+        else flush(P);
         ++jb;
     };
+    auto add = [&](CT(&U)[8], CT(&V)[8], const R* pv, CT t) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            U[k].x = fma(pv[k], t.x, U[k].x);
+            U[k].y = fma(pv[k], t.y, U[k].y);
+            V[k].x = fma(pv[8 + k], t.x, V[k].x);
+            V[k].y = fma(pv[8 + k], t.y, V[k].y);
+        }
+    };
+
+    int i_cur = it.e0 + lane < it.e1 ? ent[it.e0 + lane] : -1;
+    SwRaw<R> r_cur;
+    load_raw(i_cur, r_cur);
+    int i_nxt = it.e0 + 32 + lane < it.e1 ? ent[it.e0 + 32 + lane] : -1;
+    R* rt = rowt[w][lane];
+    for (int k = lane; k < 8 * 33; k += 32) (&colt[w][0][0])[k] = SwCol<R>{(R)0, (R)0, -1, 0};
+    __syncwarp();
+    int nbat = 0;   // batch number (tag of the column entries written by this batch)
     for (int b0 = it.e0; b0 < it.e1; b0 += 32) {
         // ---- decode slot b0 + lane
-        const int i = b0 + lane < it.e1 ? ent[b0 + lane] : -1;
-        int rx = SW_PAD, ry = 0;
+        const int i = i_cur;
+        const SwRaw<R> r = r_cur;
+        i_cur = i_nxt;
+        load_raw(i_cur, r_cur);   // next batch's inputs (their entries were loaded a batch ago)
+        i_nxt = b0 + 64 + lane < it.e1 ? ent[b0 + 64 + lane] : -1;
+        int ry = 0;
         if (i >= 0) {
             int cxv, cyv;
             R fx, fy;
             VisCoord<R>::get(a.coords, i, a.g, cxv, cyv, fx, fy);
             const int k0x = wrapn(cxv - 3, Kx, kxm);
             const int k0y = wrapn(cyv - 3, Ky, kym);
-            rx = (wrapn(k0x - c0 + 7, Kx, kxm)) - 7;     // -7 .. 31
-            ry = (wrapn(k0y - row0 + 7, Ky, kym)) - 7;   // -7 .. H - 1
+            const int rx = (wrapn(k0x - c0 + 7, Kx, kxm)) - 7;     // -7 .. 31
+            ry = (wrapn(k0y - row0 + 7, Ky, kym)) - 7;              // -7 .. H - 1
             CT val;
             if (MODE == GIN_CALLER) {
-                val = a.in[a.perm[i]];
+                val = a.in[r.p];
             } else if (MODE == GIN_SORTED) {
-                val = a.in[i];
+                val = cx<R>(r.v.x, r.v.y);
             } else {   // GIN_PD: v = U^{1/2} d max(0, 1 - eps / rho); the item holding the window start stores it
-                val = cscale(a.d[i], a.scale[a.blk ? a.blk[i] : it.l]);
-                if (a.u) val = cscale(val, sqrt(a.u[i]));
+                val = cscale(cx<R>(r.v.x, r.v.y), a.scale[a.blk ? r.p : it.l]);
+                if (a.u) val = cscale(val, sqrt(r.u));
                 if (rx >= 0 && ry >= 0 && ry < H) a.v[i] = val;
             }
-            if (a.w) val = cscale(val, a.w[i]);
-            const R su = (R)2 * fx - (R)1, sv = (R)2 * fy - (R)1;
+            if (a.w) val = cscale(val, r.w);
             R pu[8], pv[8];
+            taps((R)2 * fx - (R)1, pu);   // phi_u of window columns 0 .. 7
+            taps((R)2 * fy - (R)1, pv);   // phi_v of window rows 0 .. 7
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const R* cf = skb + (7 - m) * NC;
-                pu[m] = horner<R, NC>(cf, su);   // phi_u of window column m
-                pv[m] = horner<R, NC>(cf, sv);   // phi_v of window row m
-            }
-            R* sl = st + lane * SW_LD;
-#pragma unroll
-            for (int m = 0; m < 8; ++m) sl[m] = pu[m];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) sl[8 + k] = (R)0;
-            R* sr = sl + 8 + (ry & 7);   // row m of the window is row (ry & 7) + m of A, B
+            for (int k = 0; k < (int)sizeof(R); ++k)   // 16 reals
+                reinterpret_cast<float4*>(rt)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            R* sr = rt + (ry & 7);   // row m of the window is row (ry & 7) + m of the band pair
 #pragma unroll
             for (int m = 0; m < 8; ++m) sr[m] = pv[m];
-            sl[24] = val.x;
-            sl[25] = val.y;
+            const int g = lane >> 2;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int c = rx + m;
+                if ((unsigned)c < 32u)
+                    colt[w][g][c] = SwCol<R>{pu[m] * val.x, pu[m] * val.y, (nbat << 2) | (lane & 3), 0};
+            }
         }
-        sxs[w][lane] = rx;
         if ((lane & 3) == 0) sjb[w][lane >> 2] = ry >> 3;
         __syncwarp();
         // ---- add the batch's groups
+        // (each group's column entry and band are read one group ahead)
         const int ng = min(8, (it.e1 - b0) >> 2);
+        SwCol<R> ce_n = colt[w][0][lane];
+        int gj_n = sjb[w][0];
         for (int q = 0; q < ng; ++q) {
-            const int gj = sjb[w][q];
-            while (jb < gj) advance();
-            // the group's slots start in increasing columns and cover disjoint lanes
-            const int4 xs = reinterpret_cast<const int4*>(sxs[w])[q];
-            const int sel = (lane >= xs.y) + (lane >= xs.z) + (lane >= xs.w);
-            const int sx = sxs[w][4 * q + sel];
-            const int dx = lane - sx;
-            const R* sl = st + (4 * q + sel) * SW_LD;
-            const R pu = (unsigned)dx < 8u ? sl[dx] : (R)0;
-            R vv[4];
-            sw_ld4(sl + 24, vv);
-            const R pr = pu * vv[0], pi = pu * vv[1];
+            const SwCol<R> ce = ce_n;
+            const int gj = gj_n;
+            const bool cur = (ce.slot >> 2) == nbat;
+            const R* pvs = rowt[w][4 * q + (cur ? (ce.slot & 3) : 0)];
             R pv[16];
 #pragma unroll
-            for (int k = 0; k < 16; k += 4) sw_ld4(sl + 8 + k, pv + k);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                A[k].x = fma(pv[k], pr, A[k].x);
-                A[k].y = fma(pv[k], pi, A[k].y);
-                B[k].x = fma(pv[8 + k], pr, B[k].x);
-                B[k].y = fma(pv[8 + k], pi, B[k].y);
-            }
+            for (int k = 0; k < 16; k += 4) sw_ld4(pvs + k, pv + k);
+            const int qn = min(q + 1, 7);
+            ce_n = colt[w][qn][lane];
+            gj_n = sjb[w][qn];
+            while (jb < gj) advance();
+            const CT t = cur ? cx<R>(ce.pr, ce.pi) : cx<R>(0, 0);
+            if (jb & 1) add(Q, P, pv, t);
+            else add(P, Q, pv, t);
         }
         __syncwarp();
+        ++nbat;
     }
     while (8 * jb < H) advance();
 }
@@ -703,6 +780,13 @@ template <typename R> static NufftK<R> base_args(Plan* p) {
     k.u = (const R*)p->u_sorted;
     k.perm = p->perm;
     k.kbc = (const R*)p->kbc;
+    const int nc = p->kb_terms;
+    for (int m = 0; m < 4; ++m)
+        for (int j = 0; j < nc; ++j) {
+            const R c = (R)p->kbc_h[(size_t)(7 - m) * nc + j];
+            if (j & 1) k.kod[m * KB_HALF + j / 2] = c;
+            else k.kev[m * KB_HALF + j / 2] = c;
+        }
     k.tile_off = p->tile_off;
     k.tile_ent = p->tile_ent;
     k.blk = p->blk_id;

@@ -716,6 +716,7 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
     std::vector<double> kbc;
     p->kb_terms = p->prec == HS_F32 ? KB_TERMS_F32 : KB_TERMS_F64;
     p->kb_fit_err = kb_poly_fit(p->J, p->beta, p->kb_terms, &kbc);
+    p->kbc_h = kbc;
     std::vector<double> cx(g.nx), cy(g.ny);
     for (int i = 0; i < g.nx; ++i) cx[i] = 1.0 / kb_phihat((double)(i - g.nx / 2) / Kx, p->J, p->beta);
     for (int i = 0; i < g.ny; ++i) cy[i] = 1.0 / kb_phihat((double)(i - g.ny / 2) / Ky, p->J, p->beta);
