@@ -512,6 +512,342 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
     tile_store<R>(cl, acc, X + l * N + t0, A + l * N + t0, nx, qy, qx, s);
 }
 
+// ---- coarse levels of one (wavelet, channel) in shared memory
+// When a level's input block fits in shared memory, one CTA per (wavelet d,
+// channel l) runs that level and every coarser one without leaving the SM: X
+// holds the level's block (top-left my x mx, row stride S), Y the intermediate
+// of the two separable passes. Row passes take lane = row and 16-byte chunks
+// along the row (S = 4 words mod 32 puts a quarter-warp's chunks in distinct
+// banks); column passes take lane = column. Every level of the tail has sides
+// that are multiples of 8, so chunks never straddle the periodic wrap.
+constexpr int TAIL_THREADS = 512;
+constexpr int TAIL_SMEM_MAX = 160 * 1024;   // bytes of X and Y together
+
+template <typename R> __host__ __device__ constexpr int tail_stride(int mx) { return mx + 16 / (int)sizeof(R); }
+template <typename R> __host__ __device__ constexpr size_t tail_smem(int my, int mx) {
+    return (size_t)2 * my * tail_stride<R>(mx) * sizeof(R);
+}
+
+// x mod n for x >= 0
+template <bool P2> __device__ __forceinline__ int modp(int x, int n) {
+    if constexpr (P2) return x & (n - 1);
+    else return x < n ? x : x % n;
+}
+
+template <typename R> __device__ __forceinline__ void ld_chunk(const R* p, R* v) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+        const double2 t = *reinterpret_cast<const double2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
+}
+
+// Copies rows [0, ry) x columns [c0, c0 + cw) of a global block (row stride gs)
+// into X (row stride S) with asynchronous copies, all in flight at once: 16-byte
+// chunks when the block is 16-byte aligned (cw, c0 multiples of the chunk), else
+// single elements. Warps take rows, lanes take chunks.
+template <typename R>
+__device__ __forceinline__ void tail_stage(R* X, int S, const R* __restrict__ g, int64_t gs, int r0, int ry,
+                                           int c0, int cw, bool chunks) {
+    constexpr int EPC = 16 / (int)sizeof(R);
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (chunks) {
+        for (int r = r0 + wy; r < r0 + ry; r += nw)
+            for (int c = c0 + EPC * lane; c < c0 + cw; c += 32 * EPC) cp_async16(X + r * S + c, g + r * gs + c);
+    } else {
+        for (int r = r0 + wy; r < r0 + ry; r += nw)
+            for (int c = c0 + lane; c < c0 + cw; c += 32) cp_async(X + r * S + c, g + r * gs + c);
+    }
+}
+
+// Work items (q, c) = (it mod m, it / m) for it = threadIdx.x, threadIdx.x +
+// blockDim.x, ... below m * nc, stepped without a division per item.
+struct TailIter {
+    int q, c, dq, dc, m;
+    __device__ __forceinline__ TailIter(int m_) : m(m_) {
+        c = threadIdx.x / m;
+        q = threadIdx.x - c * m;
+        dc = blockDim.x / m;
+        dq = blockDim.x - dc * m;
+    }
+    __device__ __forceinline__ void next() {
+        q += dq;
+        c += dc;
+        if (q >= m) {
+            q -= m;
+            ++c;
+        }
+    }
+};
+
+// Analysis along x: Y[r][k] = sum_j h[j] X[r][2k + j], Y[r][hx + k] = sum_j g[j] X[r][2k + j]
+// (columns mod mx); a work item is one row and 4 consecutive output pairs.
+template <typename R, int D, bool P2>
+__device__ __forceinline__ void tail_fwd_rows(const R* X, R* Y, int S, int my, int mx) {
+    constexpr int F = 2 * (D + 1);
+    constexpr int EPC = 16 / (int)sizeof(R);
+    constexpr int NCH = (F + 6 + EPC - 1) / EPC;
+    const int hx = mx >> 1, nck = hx >> 2;
+    for (TailIter t(my); t.c < nck; t.next()) {
+        const int r = t.q, c = t.c;
+        const R* row = X + r * S;
+        R v[NCH * EPC];
+        if (8 * c + NCH * EPC <= mx) {
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) ld_chunk(row + 8 * c + EPC * k, v + EPC * k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) ld_chunk(row + modp<P2>(8 * c + EPC * k, mx), v + EPC * k);
+        }
+        R lo[4], hi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            R a = 0, b = 0;
+#pragma unroll
+            for (int j = 0; j < F; ++j) {
+                a = fma(filt<R>(D, 0, j), v[2 * u + j], a);
+                b = fma(filt<R>(D, 1, j), v[2 * u + j], b);
+            }
+            lo[u] = a;
+            hi[u] = b;
+        }
+        st4(Y + r * S + 4 * c, lo[0], lo[1], lo[2], lo[3]);
+        st4(Y + r * S + hx + 4 * c, hi[0], hi[1], hi[2], hi[3]);
+    }
+}
+
+// Analysis along y of the row-filtered block and the subband stores; a work
+// item is one column and 4 consecutive output rows. LL goes to X (compact at
+// the top-left, the next level's input) or, at the last level, to Ad.
+template <typename R, int D, bool P2>
+__device__ __forceinline__ void tail_fwd_cols(const R* Y, R* X, int S, int my, int mx, R* __restrict__ Ad,
+                                              int nx, bool last) {
+    constexpr int F = 2 * (D + 1);
+    constexpr int NV = F + 6;
+    const int hy = my >> 1, hx = mx >> 1, ncy = hy >> 2;
+    for (TailIter t(mx); t.c < ncy; t.next()) {
+        const int x = t.q, c = t.c;
+        R v[NV];
+        if (8 * c + NV <= my) {
+            const R* col = Y + 8 * c * S + x;
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = col[k * S];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) v[k] = Y[modp<P2>(8 * c + k, my) * S + x];
+        }
+        R lo[4], hi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            R a = 0, b = 0;
+#pragma unroll
+            for (int j = 0; j < F; ++j) {
+                a = fma(filt<R>(D, 0, j), v[2 * u + j], a);
+                b = fma(filt<R>(D, 1, j), v[2 * u + j], b);
+            }
+            lo[u] = a;
+            hi[u] = b;
+        }
+        const int oy = 4 * c;
+        R* o = Ad + (int64_t)oy * nx + x;
+        if (x < hx && !last) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) X[(oy + u) * S + x] = lo[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[(int64_t)u * nx] = lo[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o[(int64_t)(hy + u) * nx] = hi[u];
+    }
+}
+
+// Synthesis along y: Y[2m + p][x] = sum_k h[2k + p] a[m - k] + g[2k + p] e[m - k]
+// with a = X[.][x] (rows 0 .. hy - 1) and e = X[hy + .][x] (rows mod hy); a work
+// item is one column and 4 consecutive coefficient rows.
+template <typename R, int D, bool P2>
+__device__ __forceinline__ void tail_inv_cols(const R* X, R* Y, int S, int my, int mx) {
+    constexpr int H = D + 1;
+    constexpr int NV = H + 3;
+    const int hy = my >> 1, ncy = hy >> 2;
+    for (TailIter it(mx); it.c < ncy; it.next()) {
+        const int x = it.q, m0 = 4 * it.c;
+        R a[NV], e[NV];
+        if (m0 >= H - 1 && m0 + 4 <= hy) {
+            const R* col = X + (m0 - (H - 1)) * S + x;
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                a[t] = col[t * S];
+                e[t] = col[(hy + t) * S];
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < NV; ++t) {
+                const int row = modp<P2>(m0 - (H - 1) + t + 8 * hy, hy);
+                a[t] = X[row * S + x];
+                e[t] = X[(hy + row) * S + x];
+            }
+        }
+        R* o = Y + 2 * m0 * S + x;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            R v0 = 0, v1 = 0;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const int t = u - k + H - 1;
+                v0 = fma(filt<R>(D, 0, 2 * k), a[t], v0);
+                v0 = fma(filt<R>(D, 1, 2 * k), e[t], v0);
+                v1 = fma(filt<R>(D, 0, 2 * k + 1), a[t], v1);
+                v1 = fma(filt<R>(D, 1, 2 * k + 1), e[t], v1);
+            }
+            o[(2 * u) * S] = v0;
+            o[(2 * u + 1) * S] = v1;
+        }
+    }
+}
+
+// Synthesis along x: out[i][2n + p] = sum_k h[2k + p] Y[i][n - k] + g[2k + p] Y[i][hx + n - k]
+// (columns mod hx); a work item is one row and 4 consecutive coefficient columns
+// (8 consecutive outputs), written to X (row stride S) or to a compact block.
+template <typename R, int D, bool P2>
+__device__ __forceinline__ void tail_inv_rows(const R* Y, R* out, int ostride, int S, int my, int mx) {
+    constexpr int H = D + 1;
+    constexpr int EPC = 16 / (int)sizeof(R);
+    constexpr int BACK = ((H - 1 + EPC - 1) / EPC) * EPC;   // chunk-aligned look-back
+    constexpr int NL = BACK + 4;                            // loaded values per half
+    constexpr int OFF = BACK - (H - 1);                     // position of coefficient n0 - H + 1
+    const int hx = mx >> 1, nck = hx >> 2;
+    for (TailIter it(my); it.c < nck; it.next()) {
+        const int i = it.q, n0 = 4 * it.c;
+        const R* row = Y + i * S;
+        R a[NL], e[NL];
+        if (n0 >= BACK && n0 + 4 <= hx) {
+#pragma unroll
+            for (int k = 0; k < NL / EPC; ++k) {
+                ld_chunk(row + n0 - BACK + EPC * k, a + EPC * k);
+                ld_chunk(row + hx + n0 - BACK + EPC * k, e + EPC * k);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NL / EPC; ++k) {
+                const int n = modp<P2>(n0 - BACK + EPC * k + 8 * hx, hx);
+                ld_chunk(row + n, a + EPC * k);
+                ld_chunk(row + hx + n, e + EPC * k);
+            }
+        }
+        R o[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            R v0 = 0, v1 = 0;
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                const int t = OFF + u - k + H - 1;
+                v0 = fma(filt<R>(D, 0, 2 * k), a[t], v0);
+                v0 = fma(filt<R>(D, 1, 2 * k), e[t], v0);
+                v1 = fma(filt<R>(D, 0, 2 * k + 1), a[t], v1);
+                v1 = fma(filt<R>(D, 1, 2 * k + 1), e[t], v1);
+            }
+            o[2 * u] = v0;
+            o[2 * u + 1] = v1;
+        }
+        R* dst = out + (int64_t)i * ostride + 8 * it.c;
+        st4(dst, o[0], o[1], o[2], o[3]);
+        st4(dst + 4, o[4], o[5], o[6], o[7]);
+    }
+}
+
+// Analysis levels lev0 .. top for one (d, l): input the compact my0 x mx0 LL of
+// level lev0 - 1 (`src`); details (and the last LL) to A[1+d] at their Mallat
+// positions.
+template <typename R, bool P2>
+__global__ void __launch_bounds__(TAIL_THREADS) k_dwt_fwd_tail(const R* __restrict__ src, R* __restrict__ A,
+                                                              int L, int ny, int nx, int my0, int mx0,
+                                                              int nlev) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int S = tail_stride<R>(mx0);
+    R* X = reinterpret_cast<R*>(smem_raw);
+    R* Y = X + my0 * S;
+    const int dr = blockIdx.x / L, l = blockIdx.x - dr * L;
+    const int d = NW - 1 - dr;   // longest filters first: the short ones fill the last wave
+    const R* in = src + ((int64_t)d * L + l) * (int64_t)my0 * mx0;
+    R* Ad = A + ((int64_t)(1 + d) * L + l) * (int64_t)ny * nx;
+    tail_stage<R>(X, S, in, mx0, 0, my0, 0, mx0, true);   // plan scratch: 16-byte aligned
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+#define HS_FTAIL(DD)                                                          \
+    for (int j = 0; j < nlev; ++j) {                                          \
+        const int my = my0 >> j, mx = mx0 >> j;                               \
+        tail_fwd_rows<R, DD, P2>(X, Y, S, my, mx);                            \
+        __syncthreads();                                                      \
+        tail_fwd_cols<R, DD, P2>(Y, X, S, my, mx, Ad, nx, j == nlev - 1);     \
+        __syncthreads();                                                      \
+    }
+    HS_DWT_DISPATCH(d, HS_FTAIL)
+#undef HS_FTAIL
+}
+
+// Synthesis levels top .. lev0 for one (d, l): the coarsest LL and every
+// level's details from A[1+d]; the reconstructed my0 x mx0 input of level lev0
+// to the compact buffer `out`.
+template <typename R, bool P2>
+__global__ void __launch_bounds__(TAIL_THREADS) k_dwt_inv_tail(const R* __restrict__ A, R* __restrict__ out,
+                                                              int L, int ny, int nx, int my0, int mx0,
+                                                              int nlev, int chunks) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int S = tail_stride<R>(mx0);
+    R* X = reinterpret_cast<R*>(smem_raw);
+    R* Y = X + my0 * S;
+    const int dr = blockIdx.x / L, l = blockIdx.x - dr * L;
+    const int d = NW - 1 - dr;   // longest filters first: the short ones fill the last wave
+    const R* Ad = A + ((int64_t)(1 + d) * L + l) * (int64_t)ny * nx;
+    R* o = out + ((int64_t)d * L + l) * (int64_t)my0 * mx0;
+#define HS_ITAIL(DD)                                                                          \
+    /* a level's details lie outside the coarser level's block, so they are fetched     \
+       while the coarser level is synthesised */                                            \
+    {                                                                                         \
+        const int my = my0 >> (nlev - 1), mx = mx0 >> (nlev - 1);                            \
+        tail_stage<R>(X, S, Ad, nx, 0, my, 0, mx, chunks != 0);                               \
+        cp_async_commit();                                                                    \
+    }                                                                                         \
+    for (int j = nlev - 1; j >= 0; --j) {                                                     \
+        const int my = my0 >> j, mx = mx0 >> j;                                               \
+        if (j > 0) {                                                                          \
+            tail_stage<R>(X, S, Ad, nx, 0, my, mx, mx, chunks != 0);                          \
+            tail_stage<R>(X, S, Ad, nx, my, my, 0, 2 * mx, chunks != 0);                      \
+            cp_async_commit();                                                                \
+            cp_async_wait<1>();                                                               \
+        } else {                                                                              \
+            cp_async_wait<0>();                                                               \
+        }                                                                                     \
+        __syncthreads();                                                                      \
+        tail_inv_cols<R, DD, P2>(X, Y, S, my, mx);                                            \
+        __syncthreads();                                                                      \
+        if (j > 0) tail_inv_rows<R, DD, P2>(Y, X, S, S, my, mx);                              \
+        else tail_inv_rows<R, DD, P2>(Y, o, mx0, S, my, mx);                                  \
+        __syncthreads();                                                                      \
+    }
+    HS_DWT_DISPATCH(d, HS_ITAIL)
+#undef HS_ITAIL
+}
+
+// First level of the shared-memory tail: the finest level lev >= 1 whose input
+// block fits (both sides multiples of 8 at every level down to the top), or 0
+// when no level qualifies.
+template <typename R> static int tail_level(const Plan* p) {
+    const int top = p->levels - 1;
+    for (int lev = 1; lev <= top; ++lev) {
+        const int my = p->g.ny >> lev, mx = p->g.nx >> lev;
+        if (tail_smem<R>(my, mx) > (size_t)TAIL_SMEM_MAX) continue;
+        for (int j = lev; j <= top; ++j)
+            if (((p->g.ny >> j) % 8) || ((p->g.nx >> j) % 8)) return 0;
+        return lev;
+    }
+    return 0;
+}
+
 static hs_status upload_filters() {
     static bool done = false;
     if (done) return HS_OK;
@@ -541,6 +877,14 @@ template <typename K> static hs_status smem_attr(K k, int bytes) {
 
 hs_status dwt_init() {
     HS_TRY(upload_filters());
+    HS_TRY(smem_attr(k_dwt_fwd_tail<float, true>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_fwd_tail<float, false>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_fwd_tail<double, true>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_fwd_tail<double, false>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_inv_tail<float, true>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_inv_tail<float, false>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_inv_tail<double, true>, TAIL_SMEM_MAX));
+    HS_TRY(smem_attr(k_dwt_inv_tail<double, false>, TAIL_SMEM_MAX));
     HS_TRY(smem_attr(k_psi_fwd_l0<float, true>, FWD_SMEM * 4));
     HS_TRY(smem_attr(k_psi_fwd_l0<double, true>, FWD_SMEM * 8));
     HS_TRY(smem_attr(k_dwt_fwd_level<float, true>, FWD_SMEM * 4));
@@ -574,11 +918,18 @@ template <typename R, bool P2> static hs_status analysis_t(Plan* p, const R* X, 
     k_psi_fwd_l0<R, P2><<<dim3(ntiles(ny, nx), L), 256, FWD_SMEM * sizeof(R), s>>>(X, A, buf[0], L, ny, nx, top == 0,
                                                                               (R)(1.0 / 3.0), pairs);
     HS_CHECK_LAUNCH();
-    for (int lev = 1; lev <= top; ++lev) {
+    const int t = tail_level<R>(p);
+    for (int lev = 1; lev <= top && (t == 0 || lev < t); ++lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
         k_dwt_fwd_level<R, P2><<<g, 256, FWD_SMEM * sizeof(R), s>>>(buf[(lev - 1) & 1], A, buf[lev & 1], L, ny, nx,
                                                                 my, mx, lev == top);
+        HS_CHECK_LAUNCH();
+    }
+    if (t > 0) {
+        const int my = ny >> t, mx = nx >> t;
+        k_dwt_fwd_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my, mx), s>>>(buf[(t - 1) & 1], A, L, ny, nx,
+                                                                                my, mx, top - t + 1);
         HS_CHECK_LAUNCH();
     }
     return HS_OK;
@@ -589,7 +940,14 @@ template <typename R, bool P2> static hs_status synthesis_t(Plan* p, const R* A,
     const int L = p->g.L, ny = p->g.ny, nx = p->g.nx;
     R* buf[2] = {(R*)p->dwt_a, (R*)p->dwt_b};
     const int top = p->levels - 1;
-    for (int lev = top; lev >= 1; --lev) {
+    const int t = tail_level<R>(p);
+    if (t > 0) {
+        const int my = ny >> t, mx = nx >> t;
+        k_dwt_inv_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my, mx), s>>>(A, buf[t & 1], L, ny, nx, my, mx,
+                                                                                top - t + 1, chunks);
+        HS_CHECK_LAUNCH();
+    }
+    for (int lev = t > 0 ? t - 1 : top; lev >= 1; --lev) {
         const int my = ny >> lev, mx = nx >> lev;
         dim3 g(ntiles(my, mx), NW * L);
         k_dwt_inv_level<R, P2><<<g, 256, INV_SMEM * sizeof(R), s>>>(A, lev == top ? nullptr : buf[(lev + 1) & 1],
