@@ -268,11 +268,11 @@ def job_rate(ms: float, steps: int, world: int, device: str = "cuda"):
 # profiles/stage_traffic.txt); the roofline each is measured against is HBM.
 LIMITER = {
     "fft_fwd": "HBM: spectrum write plus the row-pass intermediate",
-    "degrid": "instruction issue (8 lanes per visibility, window gathers from L1)",
-    "grid": "instruction issue (list decode, kernel taps, 2 x 16 FMAs per window group)",
+    "degrid": "shared-memory data pipe and instruction issue (8 lanes per visibility, staged window rows)",
+    "grid": "instruction issue and shared-memory data pipe (16 row taps per lane per window group)",
     "fft_adj": "HBM: the row-pass intermediate round trip (1.57x algorithmic bytes)",
-    "psi_fwd": "FMA issue (filter taps of 8 wavelets)",
-    "psi_adj": "FMA issue and instruction cache (8 wavelets' synthesis)",
+    "psi_fwd": "instruction issue of the first level (filter taps of 8 wavelets, staging, barriers)",
+    "psi_adj": "instruction issue of the first level; instruction fetch in the shared-memory tail",
     "gram": "instruction issue (digit split and accumulator drain per 64-pixel chunk)",
 }
 
