@@ -74,9 +74,10 @@ typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
  * a fixed order, so all are bitwise reproducible. */
 #define HS_PLAN_COMPENSATED 1u
 /* FP32 plans: form the nuclear prox's L x L Gram matrix with register-blocked
- * FMA on the CUDA cores instead of the tensor cores (tcgen05, split TF32). The
- * tensor-core form is the default; this one is kept as a comparison baseline
- * and is used anyway when a buffer is not 16-byte aligned. */
+ * FMA on the CUDA cores instead of the tensor cores (tcgen05 BF16 products of
+ * exact digit splits). Without it the autotuner picks the faster form (the
+ * tensor cores when timing is off); the CUDA-core form is also used when a
+ * buffer is not 16-byte aligned. */
 #define HS_PLAN_GRAM_FMA 2u
 /* Keep the default parameters instead of timing candidates at creation. By
  * default a plan times, on itself, the sweep-gridding row cut and list cap
@@ -86,6 +87,10 @@ typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_prec;
  * process by grid, L, visibilities, precision and flags; hs_plan_info reports
  * them and the candidate times). */
 #define HS_PLAN_NO_TUNE 4u
+/* Apply F^H in L2-sized channel chunks (the row pass of each chunk, on a stream
+ * of the plan, overlapping the next chunk's column pass) without timing it
+ * against the single pass over all channels. Same arithmetic either way. */
+#define HS_PLAN_FFT_CHUNKED 8u
 
 typedef struct hs_plan* hs_plan_t;
 typedef struct hs_pd_state* hs_pd_state_t;

@@ -519,9 +519,11 @@ hs_status fft_forward(Plan* p, const void* X, cudaStream_t s) {
 // Channels per adjoint chunk that keep a chunk's traffic within half the L2:
 // the column pass of a chunk streams its grid (Ky Kx cells per channel) and
 // writes the ny x Kx intermediate, which the row pass reads right after, so the
-// intermediate can stay on chip instead of going through HBM and back. More
-// launches, each with a shorter tail: the plan's autotuner keeps the chunked
-// form only where it measures faster (p->fft_adj_chunk, default all channels).
+// intermediate can stay on chip instead of going through HBM and back. The row
+// pass of chunk c runs on the plan's side stream, overlapping the column pass
+// of chunk c + 1 (two chunks in flight fill the L2); the plan's autotuner keeps
+// the chunked form only where it measures faster (p->fft_adj_chunk, default
+// all channels).
 int fft_adjoint_chunk(const Plan* p) {
     const int64_t per = ((int64_t)p->g.Ky * p->g.Kx + (int64_t)p->g.ny * p->g.Kx) * (int64_t)p->csize();
     const int64_t budget = g_l2_bytes > 0 ? g_l2_bytes / 2 : ((int64_t)32 << 20);
@@ -531,19 +533,33 @@ int fft_adjoint_chunk(const Plan* p) {
 hs_status fft_adjoint(Plan* p, void* X, cudaStream_t s) {
     const int L = p->g.L, C = std::max(1, std::min(L, p->fft_adj_chunk > 0 ? p->fft_adj_chunk : L));
     const int64_t gch = (int64_t)p->g.Ky * p->g.Kx, tch = (int64_t)p->g.ny * p->g.Kx, xch = p->N();
+    const bool side = C < L && p->fft_side != nullptr;
+    cudaStream_t s2 = side ? p->fft_side : s;
     for (int l0 = 0; l0 < L; l0 += C) {
         const int n = std::min(C, L - l0);
         if (p->prec == HS_F32) {
             const float2* g = (const float2*)p->grid + l0 * gch;
             float2* t = (float2*)p->tmp + l0 * tch;
             HS_TRY((launch_fft<float, 1, COL_INV>(p, g, t, n, s)));
-            HS_TRY((launch_fft<float, 1, ROW_INV>(p, t, (float*)X + l0 * xch, n, s)));
+            if (side) {
+                HS_CHECK_CUDA(cudaEventRecord(p->fft_ev_col, s));
+                HS_CHECK_CUDA(cudaStreamWaitEvent(s2, p->fft_ev_col, 0));
+            }
+            HS_TRY((launch_fft<float, 1, ROW_INV>(p, t, (float*)X + l0 * xch, n, s2)));
         } else {
             const double2* g = (const double2*)p->grid + l0 * gch;
             double2* t = (double2*)p->tmp + l0 * tch;
             HS_TRY((launch_fft<double, 1, COL_INV>(p, g, t, n, s)));
-            HS_TRY((launch_fft<double, 1, ROW_INV>(p, t, (double*)X + l0 * xch, n, s)));
+            if (side) {
+                HS_CHECK_CUDA(cudaEventRecord(p->fft_ev_col, s));
+                HS_CHECK_CUDA(cudaStreamWaitEvent(s2, p->fft_ev_col, 0));
+            }
+            HS_TRY((launch_fft<double, 1, ROW_INV>(p, t, (double*)X + l0 * xch, n, s2)));
         }
+    }
+    if (side) {
+        HS_CHECK_CUDA(cudaEventRecord(p->fft_ev_join, s2));
+        HS_CHECK_CUDA(cudaStreamWaitEvent(s, p->fft_ev_join, 0));
     }
     return HS_OK;
 }

@@ -119,6 +119,8 @@ struct Plan {
     int64_t n_sw_ent = 0;
     void* kbc = nullptr;               // 8 * kb_terms reals
     std::vector<double> kbc_h;         // the same on the host
+    cudaStream_t fft_side = nullptr;   // row passes of a chunked F^H (overlap the next chunk's column pass)
+    cudaEvent_t fft_ev_col = nullptr, fft_ev_join = nullptr;
     void* cxs = nullptr;               // nx reals (Z scale along x)
     void* cys = nullptr;               // ny reals
     void* twx = nullptr;               // Kx complex, exp(-2 pi i m / Kx)

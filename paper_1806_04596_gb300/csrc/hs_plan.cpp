@@ -94,6 +94,11 @@ static void plan_release(Plan* p, void* ptr) {
 }
 
 void plan_free(Plan* p) {
+    if (p->fft_ev_col) cudaEventDestroy(p->fft_ev_col);
+    if (p->fft_ev_join) cudaEventDestroy(p->fft_ev_join);
+    if (p->fft_side) cudaStreamDestroy(p->fft_side);
+    p->fft_ev_col = p->fft_ev_join = nullptr;
+    p->fft_side = nullptr;
     for (size_t k = 0; k < p->allocs.size(); ++k) lib_free(p->allocs[k], p->alloc_bytes[k]);
     p->allocs.clear();
     p->alloc_bytes.clear();
@@ -382,7 +387,7 @@ static hs_status autotune(Plan* p, const std::vector<int>& perm, const std::vect
         }
         p->gram_tc = p->tune_gram_ms[0] <= p->tune_gram_ms[1];
     }
-    {   // F^H: all channels in one pass pair, or L2-sized channel chunks
+    if (!(p->flags & HS_PLAN_FFT_CHUNKED)) {   // F^H: all channels in one pass pair, or L2-sized channel chunks
         const int C = fft_adjoint_chunk(p);
         if (C < L) {
             p->fft_adj_chunk = 0;
@@ -762,8 +767,12 @@ static hs_status build(Plan* p, const int64_t* vis_offsets, int nblocks, const i
     HS_TRY(plan_alloc(p, (void**)&p->sv, sizeof(double) * MAX_L_NUC));
     HS_TRY(plan_alloc(p, (void**)&p->dscal, sizeof(double) * 6 * std::max(L, 1)));
     HS_TRY(plan_alloc(p, (void**)&p->err_d, sizeof(int)));
+    HS_CHECK_CUDA(cudaStreamCreateWithFlags(&p->fft_side, cudaStreamNonBlocking));
+    HS_CHECK_CUDA(cudaEventCreateWithFlags(&p->fft_ev_col, cudaEventDisableTiming));
+    HS_CHECK_CUDA(cudaEventCreateWithFlags(&p->fft_ev_join, cudaEventDisableTiming));
     HS_CHECK_CUDA(cudaMemsetAsync(p->err_d, 0, sizeof(int), s));
     if (p->flags & HS_PLAN_GRAM_FMA) p->gram_tc = 0;
+    if (p->flags & HS_PLAN_FFT_CHUNKED) p->fft_adj_chunk = fft_adjoint_chunk(p);
     if (!(p->flags & HS_PLAN_NO_TUNE)) HS_TRY(autotune(p, perm, cellx, celly, sweep, s));
     HS_CHECK_CUDA(cudaStreamSynchronize(s));
     return HS_OK;
@@ -792,7 +801,7 @@ hs_status plan_create(Plan** out, int nx, int ny, int L, const int64_t* vis_offs
                         levels, lev, hy, hx);
     }
     if (prec != HS_F32 && prec != HS_F64) return fail(HS_ERR_ARG, "bad precision %d", (int)prec);
-    if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA | HS_PLAN_NO_TUNE))
+    if (flags & ~(unsigned)(HS_PLAN_COMPENSATED | HS_PLAN_GRAM_FMA | HS_PLAN_NO_TUNE | HS_PLAN_FFT_CHUNKED))
         return fail(HS_ERR_ARG, "unknown plan flags 0x%x", flags);
     HS_TRY(dwt_init());
     HS_TRY(fft_init());

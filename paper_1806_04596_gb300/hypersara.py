@@ -24,6 +24,7 @@ HS_F32, HS_F64 = 0, 1
 HS_PLAN_COMPENSATED = 1
 HS_PLAN_GRAM_FMA = 2
 HS_PLAN_NO_TUNE = 4
+HS_PLAN_FFT_CHUNKED = 8
 STAGES = {"fft_fwd": 0, "degrid": 1, "grid": 2, "fft_adj": 3, "psi_fwd": 4, "psi_adj": 5}
 
 _lib = None
@@ -254,11 +255,12 @@ class Plan:
     def __init__(self, nx: int, ny: int, offsets: Sequence[int], uv, weights=None, precond=None,
                  oversample: int = 2, J: int = 8, kb_beta: float = 0.0, levels: int = 4,
                  prec: str = "f32", compensated: bool = False, blocks=None, gram_fma: bool = False,
-                 autotune: bool = True):
+                 autotune: bool = True, fft_chunked: bool = False):
         """blocks: optional offsets (caller order) of intra-channel data blocks, containing
         every channel boundary (hs_plan_create_blocks). gram_fma: form the nuclear prox's
         Gram matrix on the CUDA cores instead of the tensor cores (HS_PLAN_GRAM_FMA).
-        autotune=False keeps the default parameters (HS_PLAN_NO_TUNE)."""
+        autotune=False keeps the default parameters (HS_PLAN_NO_TUNE). fft_chunked: F^H in
+        L2-sized channel chunks without timing it (HS_PLAN_FFT_CHUNKED)."""
         torch = _torch()
         lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -279,7 +281,7 @@ class Plan:
                                     off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                     _ptr(precond), oversample, J, float(kb_beta), levels,
                                     HS_F32 if prec == "f32" else HS_F64,
-                                    self._flags(compensated, gram_fma, autotune), _stream())
+                                    self._flags(compensated, gram_fma, autotune, fft_chunked), _stream())
         else:
             bo = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64))
             self.blocks = bo
@@ -288,7 +290,7 @@ class Plan:
                                            bo.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(uv), _ptr(weights),
                                            _ptr(precond), oversample, J, float(kb_beta), levels,
                                            HS_F32 if prec == "f32" else HS_F64,
-                                           self._flags(compensated, gram_fma, autotune), _stream())
+                                           self._flags(compensated, gram_fma, autotune, fft_chunked), _stream())
         _check("hs_plan_create", st)
         self.nblocks = len(self.blocks) - 1
         self.h = h
@@ -296,9 +298,9 @@ class Plan:
         self.M = int(off[-1])
 
     @staticmethod
-    def _flags(compensated: bool, gram_fma: bool, autotune: bool) -> int:
+    def _flags(compensated: bool, gram_fma: bool, autotune: bool, fft_chunked: bool = False) -> int:
         return ((HS_PLAN_COMPENSATED if compensated else 0) | (HS_PLAN_GRAM_FMA if gram_fma else 0)
-                | (0 if autotune else HS_PLAN_NO_TUNE))
+                | (0 if autotune else HS_PLAN_NO_TUNE) | (HS_PLAN_FFT_CHUNKED if fft_chunked else 0))
 
     def check(self):
         """hs_plan_check: synchronise and raise if a bounded device-side wait expired."""
