@@ -523,9 +523,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
 constexpr int TAIL_THREADS = 512;
 constexpr int TAIL_SMEM_MAX = 160 * 1024;   // bytes of X and Y together
 
-template <typename R> __host__ __device__ constexpr int tail_stride(int mx) { return mx + 16 / (int)sizeof(R); }
-template <typename R> __host__ __device__ constexpr size_t tail_smem(int my, int mx) {
-    return (size_t)2 * my * tail_stride<R>(mx) * sizeof(R);
+// Row stride of X and Y, fixed at compile time so that every shared-memory
+// address in the passes is a base plus an immediate offset: 132 floats or 66
+// doubles (4 words mod 32), for blocks at most 128 floats or 64 doubles wide.
+template <typename R> __host__ __device__ constexpr int tail_stride() { return sizeof(R) == 4 ? 132 : 66; }
+template <typename R> __host__ __device__ constexpr int tail_max_width() {
+    return tail_stride<R>() - 16 / (int)sizeof(R);
+}
+template <typename R> __host__ __device__ constexpr size_t tail_smem(int my) {
+    return (size_t)2 * my * tail_stride<R>() * sizeof(R);
 }
 
 // x mod n for x >= 0
@@ -766,7 +772,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_dwt_fwd_tail(const R* __restri
                                                               int L, int ny, int nx, int my0, int mx0,
                                                               int nlev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int S = tail_stride<R>(mx0);
+    constexpr int S = tail_stride<R>();
     R* X = reinterpret_cast<R*>(smem_raw);
     R* Y = X + my0 * S;
     const int dr = blockIdx.x / L, l = blockIdx.x - dr * L;
@@ -797,7 +803,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_dwt_inv_tail(const R* __restri
                                                               int L, int ny, int nx, int my0, int mx0,
                                                               int nlev, int chunks) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int S = tail_stride<R>(mx0);
+    constexpr int S = tail_stride<R>();
     R* X = reinterpret_cast<R*>(smem_raw);
     R* Y = X + my0 * S;
     const int dr = blockIdx.x / L, l = blockIdx.x - dr * L;
@@ -840,7 +846,7 @@ template <typename R> static int tail_level(const Plan* p) {
     const int top = p->levels - 1;
     for (int lev = 1; lev <= top; ++lev) {
         const int my = p->g.ny >> lev, mx = p->g.nx >> lev;
-        if (tail_smem<R>(my, mx) > (size_t)TAIL_SMEM_MAX) continue;
+        if (mx > tail_max_width<R>() || tail_smem<R>(my) > (size_t)TAIL_SMEM_MAX) continue;
         for (int j = lev; j <= top; ++j)
             if (((p->g.ny >> j) % 8) || ((p->g.nx >> j) % 8)) return 0;
         return lev;
@@ -928,7 +934,7 @@ template <typename R, bool P2> static hs_status analysis_t(Plan* p, const R* X, 
     }
     if (t > 0) {
         const int my = ny >> t, mx = nx >> t;
-        k_dwt_fwd_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my, mx), s>>>(buf[(t - 1) & 1], A, L, ny, nx,
+        k_dwt_fwd_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my), s>>>(buf[(t - 1) & 1], A, L, ny, nx,
                                                                                 my, mx, top - t + 1);
         HS_CHECK_LAUNCH();
     }
@@ -943,7 +949,7 @@ template <typename R, bool P2> static hs_status synthesis_t(Plan* p, const R* A,
     const int t = tail_level<R>(p);
     if (t > 0) {
         const int my = ny >> t, mx = nx >> t;
-        k_dwt_inv_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my, mx), s>>>(A, buf[t & 1], L, ny, nx, my, mx,
+        k_dwt_inv_tail<R, P2><<<NW * L, TAIL_THREADS, tail_smem<R>(my), s>>>(A, buf[t & 1], L, ny, nx, my, mx,
                                                                                 top - t + 1, chunks);
         HS_CHECK_LAUNCH();
     }

@@ -83,8 +83,9 @@ def test_pd_fp32_matches_oracle_snr_c1():
 
 
 def test_pd_graph_equals_eager():
-    """With the fixed-order (compensated) gridding the replayed graph reproduces
-    the eager launches bitwise; with shared-atomic gridding to rounding."""
+    """Every gridding form sums in a fixed order, so the replayed graph
+    reproduces the eager launches bitwise, for the compensated tiles and for the
+    default register sweep; the two forms agree to FP32 rounding."""
     inp = synth.make_inputs(1, n=64, L=3, M=(800, 1500), seed=77)
     prob, prm = _setup(inp, "f32")
     _, s1 = _gpu_state(inp, prob, prm, "f32", compensated=True)
@@ -95,8 +96,12 @@ def test_pd_graph_equals_eager():
     b = host(s2.get()[0])
     assert np.array_equal(a, b)
     _, s3 = _gpu_state(inp, prob, prm, "f32")
+    _, s4 = _gpu_state(inp, prob, prm, "f32")
     s3.solve(7, graph=True)
-    assert rel(host(s3.get()[0]), a) <= 1e-5
+    s4.solve(7, graph=False)
+    c = host(s3.get()[0])
+    assert np.array_equal(c, host(s4.get()[0]))
+    assert rel(c, a) <= 1e-5
 
 
 def test_pd_fp64_with_preconditioner_and_priors_off():
