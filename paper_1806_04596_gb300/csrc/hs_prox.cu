@@ -85,41 +85,50 @@ __global__ void __launch_bounds__(256) k_l21(const R* __restrict__ A, const R* _
     }
 }
 
-// FP32 form of k_l21 for two neighbouring pixels per thread (8-byte loads and
-// stores; N even, buffers 8-byte aligned): the same operations per row, in
-// the same order.
-template <int LMAX>
-__global__ void __launch_bounds__(128) k_l21_pairs(const float* __restrict__ A, const float* __restrict__ W,
+// FP32 form with the channels of a row split over the 4 warps of a CTA
+// (channel l to warp l mod 4): a CTA covers 32 pixel pairs of one basis, every
+// lane keeps at most LW channels of its pair in registers (LW = ceil(L / 4)),
+// and the 4 warps' partial sums of squares meet in shared memory, added in the
+// same order by every warp. With at most 16 channels of a pair per thread,
+// many more loads are in flight per SM than with a whole row per thread (the
+// kernel streams A and W once and writes the dual once).
+template <int LW>
+__global__ void __launch_bounds__(128) k_l21_split(const float* __restrict__ A, const float* __restrict__ W,
                                                    const float* __restrict__ w_rows, float thr, int dual,
                                                    float* __restrict__ out, int L, int64_t N) {
+    __shared__ float2 part[4][32];
     const int64_t Nh = N >> 1;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)NB * Nh) return;
-    const int b = (int)(t / Nh);
-    const int64_t pix = 2 * (t - (int64_t)b * Nh);
-    const int64_t base = (int64_t)b * L * N + pix;
-    float2 q[LMAX];
+    const int64_t nq = (Nh + 31) >> 5;   // CTAs per basis
+    const int b = (int)(blockIdx.x / nq);
+    const int64_t pp = (blockIdx.x - (int64_t)b * nq) * 32 + (threadIdx.x & 31);
+    const int wv = threadIdx.x >> 5;
+    const bool in = pp < Nh;
+    const int64_t base = (int64_t)b * L * N + 2 * pp;
+    float2 q[LW];
+    float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int l = 0; l < LMAX; ++l)
-        if (l < L) {
+    for (int c = 0; c < LW; ++c) {
+        const int l = wv + 4 * c;
+        if (in && l < L) {
             float2 v = *reinterpret_cast<const float2*>(A + base + (int64_t)l * N);
             if (W) {
                 const float2 u = *reinterpret_cast<const float2*>(W + base + (int64_t)l * N);
                 v.x += u.x;
                 v.y += u.y;
             }
-            q[l] = v;
+            q[c] = v;
+            s0 = fmaf(v.x, v.x, s0);
+            s1 = fmaf(v.y, v.y, s1);
         }
-    float s0 = 0, s1 = 0;
-#pragma unroll
-    for (int l = 0; l < LMAX; ++l)
-        if (l < L) {
-            s0 = fmaf(q[l].x, q[l].x, s0);
-            s1 = fmaf(q[l].y, q[l].y, s1);
-        }
-    const float n0 = sqrtf(s0), n1 = sqrtf(s1);
+    }
+    part[wv][threadIdx.x & 31] = make_float2(s0, s1);
+    __syncthreads();
+    if (!in) return;
+    const float2 p0 = part[0][threadIdx.x & 31], p1 = part[1][threadIdx.x & 31];
+    const float2 p2 = part[2][threadIdx.x & 31], p3 = part[3][threadIdx.x & 31];
+    const float n0 = sqrtf((p0.x + p1.x) + (p2.x + p3.x)), n1 = sqrtf((p0.y + p1.y) + (p2.y + p3.y));
     float2 wr = make_float2(1.f, 1.f);
-    if (w_rows) wr = *reinterpret_cast<const float2*>(w_rows + (int64_t)b * N + pix);
+    if (w_rows) wr = *reinterpret_cast<const float2*>(w_rows + (int64_t)b * N + 2 * pp);
     const float lam0 = thr * wr.x, lam1 = thr * wr.y;
     float f0, f1;
     if (dual == 2) {   // direction: gradient of lam ||q||
@@ -133,8 +142,11 @@ __global__ void __launch_bounds__(128) k_l21_pairs(const float* __restrict__ A, 
         f1 = (n1 > lam1) ? (n1 - lam1) / n1 : 0.f;
     }
 #pragma unroll
-    for (int l = 0; l < LMAX; ++l)
-        if (l < L) *reinterpret_cast<float2*>(out + base + (int64_t)l * N) = make_float2(q[l].x * f0, q[l].y * f1);
+    for (int c = 0; c < LW; ++c) {
+        const int l = wv + 4 * c;
+        if (l < L)
+            *reinterpret_cast<float2*>(out + base + (int64_t)l * N) = make_float2(q[c].x * f0, q[c].y * f1);
+    }
 }
 
 template <typename R>
@@ -169,12 +181,13 @@ hs_status l21_apply(Plan* p, const void* A, const void* Wadd, const void* w_rows
     auto al8 = [](const void* q) { return ((uintptr_t)q % 8) == 0; };
     const bool pairs = (N % 2) == 0 && al8(A) && al8(Wadd) && al8(w_rows) && al8(out);
     if (p->prec == HS_F32 && pairs && L <= 64) {
-        const unsigned g2 = nblk((int64_t)NB * (N / 2), 128);
+        const int64_t nq = (N / 2 + 31) / 32;
+        const unsigned g2 = (unsigned)(NB * nq);
         if (L <= 16)
-            k_l21_pairs<16><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
-                                               (float)thr, dual, (float*)out, L, N);
+            k_l21_split<4><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
+                                              (float)thr, dual, (float*)out, L, N);
         else
-            k_l21_pairs<64><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
+            k_l21_split<16><<<g2, 128, 0, s>>>((const float*)A, (const float*)Wadd, (const float*)w_rows,
                                                (float)thr, dual, (float*)out, L, N);
     } else if (p->prec == HS_F32) {
         if (L <= 16) HS_L21(float, 16);
@@ -565,11 +578,87 @@ __global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X
         if (i < L) out[(int64_t)i * N + n] = z[i];
 }
 
+// FP32 form with the channels of a pixel split over the 4 warps of a CTA
+// (channel i to warp i mod 4; 32 pixels per CTA): each warp forms partial
+// projections of its channels on 8 components at a time, the partials meet in
+// shared memory (added in the same order by every warp), and every lane then
+// updates its own channels in component order, as in k_lowrank_apply. At most
+// LW = ceil(L / 4) channels per lane in registers, so far more pixels are in
+// flight per SM than with one pixel's whole spectrum per thread.
+constexpr int LRS_CC = 8;   // components per shared-memory round
+template <int LW>
+__global__ void __launch_bounds__(128) k_lowrank_split(const float* __restrict__ X, const float* __restrict__ Xa,
+                                                       const double* __restrict__ F, int L, int64_t N,
+                                                       float* __restrict__ out) {
+    __shared__ float2 part[LRS_CC][4][32];
+    const int r = (int)F[LR_R];
+    const bool base = F[LR_BASE] != 0.0;
+    const float* Ff = reinterpret_cast<const float*>(F + LR_DOUBLES);
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int64_t n = blockIdx.x * (int64_t)32 + lane;
+    const bool in = n < N;
+    float z[LW], acc[LW];
+#pragma unroll
+    for (int k = 0; k < LW; ++k) {
+        const int i = wv + 4 * k;
+        z[k] = 0.f;
+        if (in && i < L) {
+            z[k] = X[(int64_t)i * N + n];
+            if (Xa) z[k] += Xa[(int64_t)i * N + n];
+        }
+        acc[k] = base ? z[k] : 0.f;
+    }
+    for (int c0 = 0; c0 < r; c0 += LRS_CC) {
+        const int nc = min(LRS_CC, r - c0);
+        for (int cc = 0; cc < nc; ++cc) {
+            const int c = c0 + cc;
+            float p = 0.f, p2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < LW; ++k) {
+                const int i = wv + 4 * k;
+                if (i < L) {
+                    p = fmaf(z[k], Ff[LRF_XH + c * MAX_L_NUC + i], p);
+                    p2 = fmaf(z[k], Ff[LRF_XL + c * MAX_L_NUC + i], p2);
+                }
+            }
+            part[cc][wv][lane] = make_float2(p, p2);
+        }
+        __syncthreads();
+        for (int cc = 0; cc < nc; ++cc) {
+            const int c = c0 + cc;
+            const float2 a = part[cc][0][lane], b = part[cc][1][lane], d = part[cc][2][lane], e = part[cc][3][lane];
+            const float q = Ff[LRF_G + c] * (((a.x + b.x) + (d.x + e.x)) + ((a.y + b.y) + (d.y + e.y)));
+#pragma unroll
+            for (int k = 0; k < LW; ++k) {
+                const int i = wv + 4 * k;
+                if (i < L) {
+                    acc[k] = fmaf(q, Ff[LRF_XH + c * MAX_L_NUC + i], acc[k]);
+                    acc[k] = fmaf(q, Ff[LRF_XL + c * MAX_L_NUC + i], acc[k]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!in) return;
+#pragma unroll
+    for (int k = 0; k < LW; ++k) {
+        const int i = wv + 4 * k;
+        if (i < L) out[(int64_t)i * N + n] = acc[k];
+    }
+}
+
 template <typename R>
 static hs_status lowrank_apply_t(Plan* p, const void* X, const void* Xa, void* out, cudaStream_t s) {
     const int L = p->g.L;
     const int64_t N = p->N();
     const unsigned g = nblk(N, LR_BS);
+    if constexpr (sizeof(R) == 4) {
+        const unsigned g4 = (unsigned)((N + 31) / 32);
+        if (L <= 16) k_lowrank_split<4><<<g4, 128, 0, s>>>((const float*)X, (const float*)Xa, p->eigf, L, N, (float*)out);
+        else k_lowrank_split<16><<<g4, 128, 0, s>>>((const float*)X, (const float*)Xa, p->eigf, L, N, (float*)out);
+        HS_CHECK_LAUNCH();
+        return HS_OK;
+    }
 #define HS_LR(LM) \
     k_lowrank_apply<R, LM><<<g, LR_BS, 0, s>>>((const R*)X, (const R*)Xa, p->eigf, L, N, (R*)out)
     if (L <= 8) HS_LR(8);
