@@ -269,7 +269,7 @@ def job_rate(ms: float, steps: int, world: int, device: str = "cuda"):
 LIMITER = {
     "fft_fwd": "HBM: spectrum write plus the row-pass intermediate",
     "degrid": "shared-memory data pipe and instruction issue (8 lanes per visibility, staged window rows)",
-    "grid": "instruction issue and shared-memory data pipe (16 row taps per lane per window group)",
+    "grid": "instruction issue and shared-memory data pipe (12 row taps per lane per window group)",
     "fft_adj": "HBM: the row-pass intermediate round trip (1.57x algorithmic bytes)",
     "psi_fwd": "instruction issue of the first level (filter taps of 8 wavelets, staging, barriers)",
     "psi_adj": "instruction issue of the first level; instruction fetch in the shared-memory tail",

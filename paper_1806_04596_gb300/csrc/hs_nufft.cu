@@ -533,18 +533,18 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
 
 // Sweep gridding (grids of at least 64 x 64 cells, default kernel). A warp owns
 // one work item of the plan: a 32-column strip of one channel's grid and its
-// output rows [row0, row1). Lane c holds column c of two 8-row register banks P
-// and Q; band j (rows 8j .. 8j + 7 relative to row0) lives in P for even j and
-// in Q for odd j. The warp walks the item's groups band by band: a group holds
-// up to 4 windows with disjoint columns starting in band j, so they lie in
-// bands j and j + 1 and one pass over the 16 rows (2 x 16 FMAs per lane) adds
-// them; once a group of a later band arrives, band j is final, so its bank is
-// stored (each output cell once, coalesced 256-byte rows) and cleared for band
-// j + 2. The banks never move between registers, there is no shared-memory
-// read-modify-write, no atomics, and the summation order is fixed.
+// output rows [row0, row1). Lane c holds column c of three 4-row register
+// banks; band j (rows 4j .. 4j + 3 relative to row0) lives in bank j mod 3. The
+// warp walks the item's groups band by band: a group holds up to 4 windows with
+// disjoint columns starting in band j, so they lie in bands j .. j + 2 and one
+// pass over those 12 rows (2 x 12 FMAs per lane) adds them; once a group of a
+// later band arrives, band j is final, so its bank is stored (each output cell
+// once, coalesced 256-byte rows) and cleared for band j + 3. The banks never
+// move between registers, there is no shared-memory read-modify-write, no
+// atomics, and the summation order is fixed.
 // Lists are consumed in batches of 32 slots (8 groups): lane q decodes slot q
 // (window position, weighted value, the 16 kernel taps) into shared memory: the
-// 8 row taps at their rows of the 16-row window (zeros elsewhere), and for
+// 8 row taps at their rows of the 12-row span (zeros elsewhere), and for
 // every strip column the window covers, the column tap times the value and the
 // slot's place in its group, tagged with the batch number (a column whose entry
 // carries an older tag has no window in the group and adds zero, so the table
@@ -583,9 +583,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
                  const int* __restrict__ ent, int n_items) {
     typedef Cx<R> CT;
     constexpr int NE = (NC + 1) / 2, NO = NC / 2;   // even / odd coefficients of a piece
-    // row taps of every slot, placed at their rows; the row stride (20 floats, 18
-    // doubles) puts the 4 slots of a group in disjoint banks for 16-byte loads
-    constexpr int RLD = sizeof(R) == 4 ? 20 : 18;
+    // row taps of every slot, placed at their rows; with 12 reals per slot the 4
+    // slots of a group fall in disjoint banks for 16-byte loads
+    constexpr int RLD = 12;
     __shared__ __align__(16) R rowt[SW_WARPS][32][RLD];
     // per group and strip column (rows padded to 33 entries: the decode's scattered
     // 16-byte stores of different groups fall in different banks)
@@ -599,10 +599,11 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
     const int kxm = a.g.kxm, kym = a.g.kym;
     const int c0 = it.strip * GRID_TILE, row0 = it.row0, H = it.row1 - it.row0;
     CT* out = a.grid_out + (int64_t)it.l * Ky * Kx + (int64_t)row0 * Kx + c0 + lane;
-    CT P[8], Q[8];
+    CT B0[4], B1[4], B2[4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) P[k] = Q[k] = cx<R>(0, 0);
-    int jb = -1;   // band whose rows are final next (rows -8 .. -1 are never stored)
+    for (int k = 0; k < 4; ++k) B0[k] = B1[k] = B2[k] = cx<R>(0, 0);
+    int jb = -2;   // band whose rows are final next (rows -8 .. -1 are never stored)
+    int jm = 1;    // its bank, jb mod 3
 
     // ---- loads of one slot's inputs (list entry i, -1 = padding)
     auto load_raw = [&](int i, SwRaw<R>& r) {
@@ -638,26 +639,30 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
         }
     };
     // ---- store the final band jb (rows 8 jb .. 8 jb + 7 inside [0, H)) and clear its bank
-    auto flush = [&](CT(&U)[8]) {
+    auto flush = [&](CT(&U)[4]) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = 8 * jb + k;
+        for (int k = 0; k < 4; ++k) {
+            const int r = 4 * jb + k;
             if ((unsigned)r < (unsigned)H) out[(int64_t)r * Kx] = U[k];
             U[k] = cx<R>(0, 0);
         }
     };
     auto advance = [&]() {
-        if (jb & 1) flush(Q);
-        else flush(P);
+        if (jm == 0) flush(B0);
+        else if (jm == 1) flush(B1);
+        else flush(B2);
         ++jb;
+        jm = jm == 2 ? 0 : jm + 1;
     };
-    auto add = [&](CT(&U)[8], CT(&V)[8], const R* pv, CT t) {
+    auto add = [&](CT(&U)[4], CT(&V)[4], CT(&W)[4], const R* pv, CT t) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < 4; ++k) {
             U[k].x = fma(pv[k], t.x, U[k].x);
             U[k].y = fma(pv[k], t.y, U[k].y);
-            V[k].x = fma(pv[8 + k], t.x, V[k].x);
-            V[k].y = fma(pv[8 + k], t.y, V[k].y);
+            V[k].x = fma(pv[4 + k], t.x, V[k].x);
+            V[k].y = fma(pv[4 + k], t.y, V[k].y);
+            W[k].x = fma(pv[8 + k], t.x, W[k].x);
+            W[k].y = fma(pv[8 + k], t.y, W[k].y);
         }
     };
 
@@ -700,9 +705,9 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
             taps((R)2 * fx - (R)1, pu);   // phi_u of window columns 0 .. 7
             taps((R)2 * fy - (R)1, pv);   // phi_v of window rows 0 .. 7
 #pragma unroll
-            for (int k = 0; k < (int)sizeof(R); ++k)   // 16 reals
+            for (int k = 0; k < 3 * (int)sizeof(R) / 4; ++k)   // 12 reals
                 reinterpret_cast<float4*>(rt)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            R* sr = rt + (ry & 7);   // row m of the window is row (ry & 7) + m of the band pair
+            R* sr = rt + (ry & 3);   // row m of the window is row (ry & 3) + m of the three bands
 #pragma unroll
             for (int m = 0; m < 8; ++m) sr[m] = pv[m];
             const int g = lane >> 2;
@@ -713,7 +718,7 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
                     colt[w][g][c] = SwCol<R>{pu[m] * val.x, pu[m] * val.y, (nbat << 2) | (lane & 3), 0};
             }
         }
-        if ((lane & 3) == 0) sjb[w][lane >> 2] = ry >> 3;
+        if ((lane & 3) == 0) sjb[w][lane >> 2] = ry >> 2;
         __syncwarp();
         // ---- add the batch's groups
         // (each group's column entry and band are read one group ahead)
@@ -725,21 +730,22 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
             const int gj = gj_n;
             const bool cur = (ce.slot >> 2) == nbat;
             const R* pvs = rowt[w][4 * q + (cur ? (ce.slot & 3) : 0)];
-            R pv[16];
+            R pv[12];
 #pragma unroll
-            for (int k = 0; k < 16; k += 4) sw_ld4(pvs + k, pv + k);
+            for (int k = 0; k < 12; k += 4) sw_ld4(pvs + k, pv + k);
             const int qn = min(q + 1, 7);
             ce_n = colt[w][qn][lane];
             gj_n = sjb[w][qn];
             while (jb < gj) advance();
             const CT t = cur ? cx<R>(ce.pr, ce.pi) : cx<R>(0, 0);
-            if (jb & 1) add(Q, P, pv, t);
-            else add(P, Q, pv, t);
+            if (jm == 0) add(B0, B1, B2, pv, t);
+            else if (jm == 1) add(B1, B2, B0, pv, t);
+            else add(B2, B0, B1, pv, t);
         }
         __syncwarp();
         ++nbat;
     }
-    while (8 * jb < H) advance();
+    while (4 * jb < H) advance();
 }
 
 // Sum of the partial tiles of every split tile (fixed slot order).

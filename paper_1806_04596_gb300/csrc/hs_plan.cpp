@@ -158,8 +158,8 @@ static hs_status download_real(const Plan* p, const void* src, int64_t n, std::v
 // its list holds every window that overlaps the strip and starts in rows
 // row0 - 7 .. row1 - 1 (circularly), as groups of 4 slots (-1 pads) whose
 // windows cover disjoint columns of the strip (slots in increasing start
-// column) and start in the same 8-row band (relative start row y, band
-// floor(y / 8)), so that they all lie in that band and the next. Windows are
+// column) and start in the same 4-row band (relative start row y, band
+// floor(y / 4)), so that they all lie in that band and the next two. Windows are
 // placed in increasing start row, first fit over the band's groups; groups are
 // stored by band. Rows are cut after hmax rows, or earlier once the list
 // would pass cap windows (at least one row per item). Items are stored
@@ -228,7 +228,7 @@ hs_status sweep_lists(int Kx, int Ky, int L, const int64_t* off, const int* k0xs
                 for (const Win& w : seg) {
                     const int b = std::max(w.x, 0), e = std::min(w.x + 8, GRID_TILE);
                     const uint32_t mask = (uint32_t)(((uint64_t)1 << e) - ((uint64_t)1 << b));
-                    const int band = (w.y + 8) / 8 - 1;   // floor(y / 8), y >= -7
+                    const int band = (w.y + 8) / 4 - 2;   // floor(y / 4), y >= -7
                     while (first < open.size() && open[first].y < band) ++first;
                     size_t gi = first;
                     while (gi < open.size() && (open[gi].m == 4 || (open[gi].mask & mask))) ++gi;

@@ -1,6 +1,6 @@
 """Host logic of the sweep gridding (G_l^H, Sec. 2.1, step 12) on the CPU:
 the work lists the plan builds (hs_sweep_lists) satisfy the conditions the
-kernel relies on, and the kernel's algorithm run on them in NumPy (two 8-row
+kernel relies on, and the kernel's algorithm run on them in NumPy (three 4-row
 register bands per 32-column strip, groups of windows with disjoint columns)
 equals direct gridding of the same windows."""
 
@@ -57,8 +57,8 @@ def test_lists_meet_the_kernel_conditions(Kx, Ky, hmax_req, cap):
             assert np.all((real >= off[l]) & (real < off[l + 1]))
             ry = _rel_row(k0y[real], r0, Ky)
             rx = _rel_col(k0x[real], c0, Kx)
-            band = ry[0] // 8
-            assert np.all(ry // 8 == band) and band >= band_prev
+            band = ry[0] // 4
+            assert np.all(ry // 4 == band) and band >= band_prev
             band_prev = band
             lo, hi = np.maximum(rx, 0), np.minimum(rx + 8, T)
             assert np.all(np.diff(rx) > 0) and np.all(lo[1:] >= hi[:-1])   # disjoint, by column
@@ -93,24 +93,25 @@ def test_sweep_on_the_lists_equals_direct_gridding(hmax_req, cap):
     lanes = np.arange(T)
     for (l, s, r0, r1, e0, e1) in items:
         c0, H = s * T, r1 - r0
-        A = np.zeros((8, T), complex)
-        B = np.zeros((8, T), complex)
-        jb = -1
+        banks = [np.zeros((4, T), complex) for _ in range(3)]   # band j in bank j mod 3
+        jb = -2
 
         def advance():
-            nonlocal A, B, jb
-            for k in range(8):
-                r = 8 * jb + k
+            nonlocal jb
+            A = banks[jb % 3]
+            for k in range(4):
+                r = 4 * jb + k
                 if 0 <= r < H:
                     assert np.all(np.isnan(out[l, r0 + r, c0:c0 + T]))   # every cell stored once
                     out[l, r0 + r, c0:c0 + T] = A[k]
-            A, B, jb = B, np.zeros((8, T), complex), jb + 1
+            A[:] = 0
+            jb += 1
 
         for g in range(e0, e1, 4):
             slots = ent[g:g + 4]
             rx = np.array([_rel_col(k0x[i], c0, Kx) if i >= 0 else 1 << 20 for i in slots])
             ry0 = _rel_row(k0y[slots[0]], r0, Ky)
-            while jb < ry0 // 8:
+            while jb < ry0 // 4:
                 advance()
             sel = (lanes >= rx[1]).astype(int) + (lanes >= rx[2]) + (lanes >= rx[3])
             for lane in range(T):
@@ -118,11 +119,10 @@ def test_sweep_on_the_lists_equals_direct_gridding(hmax_req, cap):
                 dx = lane - rx[sel[lane]]
                 if not 0 <= dx < 8:
                     continue
-                o = _rel_row(k0y[i], r0, Ky) & 7
+                o = _rel_row(k0y[i], r0, Ky) & 3
                 for m in range(8):
-                    band = A if o + m < 8 else B
-                    band[(o + m) & 7, lane] += val[i] * phy[i, m] * phx[i, dx]
-        while 8 * jb < H:
+                    banks[(jb + (o + m) // 4) % 3][(o + m) & 3, lane] += val[i] * phy[i, m] * phx[i, dx]
+        while 4 * jb < H:
             advance()
     assert not np.isnan(out).any()
     assert np.max(np.abs(out - ref)) <= 1e-12 * np.max(np.abs(ref))
