@@ -548,7 +548,8 @@ __global__ void __launch_bounds__(GRID_PW * 32) k_grid_groups(NufftK<R> a, const
 // every strip column the window covers, the column tap times the value and the
 // slot's place in its group, tagged with the batch number (a column whose entry
 // carries an older tag has no window in the group and adds zero, so the table
-// is never cleared), and the group pass reads one 16-byte entry per lane. The
+// is never cleared), and the group pass reads one 8-byte value and one 4-byte
+// tag per lane. The
 // next batch's list entries and inputs are loaded before the current batch's
 // groups are added.
 constexpr int SW_WARPS = 4;      // warps (work items) per CTA
@@ -562,13 +563,6 @@ __device__ __forceinline__ void sw_ld4(const double* p, double* v) {
     const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
     v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
 }
-
-// Column entry of a group: column tap x value of the window covering the
-// column and, in `slot`, 4 x the batch number + that window's slot in the group.
-template <typename R> struct __align__(16) SwCol {
-    R pr, pi;
-    int slot, pad;
-};
 
 // Inputs of one list slot loaded ahead of its decoding.
 template <typename R> struct SwRaw {
@@ -587,9 +581,11 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
     // slots of a group fall in disjoint banks for 16-byte loads
     constexpr int RLD = 12;
     __shared__ __align__(16) R rowt[SW_WARPS][32][RLD];
-    // per group and strip column (rows padded to 33 entries: the decode's scattered
-    // 16-byte stores of different groups fall in different banks)
-    __shared__ __align__(16) SwCol<R> colt[SW_WARPS][8][33];
+    // per group and strip column: column tap x value, and 4 x batch + slot in the
+    // group (rows padded to 33 entries: the decode's scattered stores of different
+    // groups fall in different banks)
+    __shared__ __align__(16) CT coltv[SW_WARPS][8][33];
+    __shared__ int coltg[SW_WARPS][8][33];
     __shared__ int sjb[SW_WARPS][8];                          // band of every group
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wi = blockIdx.x * SW_WARPS + w;
@@ -671,7 +667,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
     load_raw(i_cur, r_cur);
     int i_nxt = it.e0 + 32 + lane < it.e1 ? ent[it.e0 + 32 + lane] : -1;
     R* rt = rowt[w][lane];
-    for (int k = lane; k < 8 * 33; k += 32) (&colt[w][0][0])[k] = SwCol<R>{(R)0, (R)0, -1, 0};
+    for (int k = lane; k < 8 * 33; k += 32) {
+        (&coltv[w][0][0])[k] = cx<R>(0, 0);
+        (&coltg[w][0][0])[k] = -1;
+    }
     __syncwarp();
     int nbat = 0;   // batch number (tag of the column entries written by this batch)
     for (int b0 = it.e0; b0 < it.e1; b0 += 32) {
@@ -715,7 +714,10 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
             for (int m = 0; m < 8; ++m) {
                 const int c = rx + m;
                 if ((unsigned)c < 32u)
-                    colt[w][g][c] = SwCol<R>{pu[m] * val.x, pu[m] * val.y, (nbat << 2) | (lane & 3), 0};
+                {
+                    coltv[w][g][c] = cx<R>(pu[m] * val.x, pu[m] * val.y);
+                    coltg[w][g][c] = (nbat << 2) | (lane & 3);
+                }
             }
         }
         if ((lane & 3) == 0) sjb[w][lane >> 2] = ry >> 2;
@@ -723,21 +725,24 @@ __global__ void __launch_bounds__(SW_WARPS * 32, sizeof(R) == 4 ? 5 : 1)
         // ---- add the batch's groups
         // (each group's column entry and band are read one group ahead)
         const int ng = min(8, (it.e1 - b0) >> 2);
-        SwCol<R> ce_n = colt[w][0][lane];
+        CT cv_n = coltv[w][0][lane];
+        int cg_n = coltg[w][0][lane];
         int gj_n = sjb[w][0];
         for (int q = 0; q < ng; ++q) {
-            const SwCol<R> ce = ce_n;
+            const CT cv = cv_n;
+            const int cg = cg_n;
             const int gj = gj_n;
-            const bool cur = (ce.slot >> 2) == nbat;
-            const R* pvs = rowt[w][4 * q + (cur ? (ce.slot & 3) : 0)];
+            const bool cur = (cg >> 2) == nbat;
+            const R* pvs = rowt[w][4 * q + (cur ? (cg & 3) : 0)];
             R pv[12];
 #pragma unroll
             for (int k = 0; k < 12; k += 4) sw_ld4(pvs + k, pv + k);
             const int qn = min(q + 1, 7);
-            ce_n = colt[w][qn][lane];
+            cv_n = coltv[w][qn][lane];
+            cg_n = coltg[w][qn][lane];
             gj_n = sjb[w][qn];
             while (jb < gj) advance();
-            const CT t = cur ? cx<R>(ce.pr, ce.pi) : cx<R>(0, 0);
+            const CT t = cur ? cv : cx<R>(0, 0);
             if (jm == 0) add(B0, B1, B2, pv, t);
             else if (jm == 1) add(B1, B2, B0, pv, t);
             else add(B2, B0, B1, pv, t);
