@@ -281,10 +281,12 @@ __global__ void __launch_bounds__(EIG_T) k_eig_mixed(const double* __restrict__ 
     if (tid == 0) r_act = 0;
     __syncthreads();
     if (tid < L) {   // rank of eigenvalue tid; active when sigma > c_rank (1 - 1e-3)
+        // a NaN (from a non-finite input) ranks below every number, so the ranks stay a
+        // permutation and every index taken from `order` stays in range
         int rk = 0;
-        const float li = lamf[tid];
+        const float li = isnan(lamf[tid]) ? -INFINITY : lamf[tid];
         for (int j = 0; j < L; ++j) {
-            const float lj = lamf[j];
+            const float lj = isnan(lamf[j]) ? -INFINITY : lamf[j];
             rk += (lj > li) || (lj == li && j < tid);
         }
         order[rk] = tid;
@@ -472,10 +474,13 @@ __global__ void __launch_bounds__(EIG_T) k_eig_f64(const double* __restrict__ Sg
     jacobi_n<double>(n, A, B, V, W, partner, 1e-17, 1e-18, 1e-16, 40, cs, red, &flag);
     if (tid < L) lam[tid] = A[tid * LD32 + tid];
     __syncthreads();
-    if (tid < L) {
+    if (tid < L) {   // NaN ranks last (the ranks stay a permutation)
         int rk = 0;
-        const double li = lam[tid];
-        for (int j = 0; j < L; ++j) rk += (lam[j] > li) || (lam[j] == li && j < tid);
+        const double li = isnan(lam[tid]) ? -INFINITY : lam[tid];
+        for (int j = 0; j < L; ++j) {
+            const double lj = isnan(lam[j]) ? -INFINITY : lam[j];
+            rk += (lj > li) || (lj == li && j < tid);
+        }
         order[rk] = tid;
     }
     __syncthreads();

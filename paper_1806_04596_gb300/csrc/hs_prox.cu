@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(LR_BS) k_lowrank_apply(const R* __restrict__ X
                                                          R* __restrict__ out) {
     constexpr bool SPLIT = sizeof(R) == 4;
     __shared__ R qs[LMAX * LR_BS];
-    const int r = (int)F[LR_R];
+    const int r = max(0, min((int)F[LR_R], L));   // the active count, always <= L
     const bool base = F[LR_BASE] != 0.0;
     const float* Ff = reinterpret_cast<const float*>(F + LR_DOUBLES);
     const int t = threadIdx.x;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) k_lowrank_split(const float* __restrict__
                                                        const double* __restrict__ F, int L, int64_t N,
                                                        float* __restrict__ out) {
     __shared__ float2 part[LRS_CC][4][32];
-    const int r = (int)F[LR_R];
+    const int r = max(0, min((int)F[LR_R], L));   // the active count, always <= L
     const bool base = F[LR_BASE] != 0.0;
     const float* Ff = reinterpret_cast<const float*>(F + LR_DOUBLES);
     const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
