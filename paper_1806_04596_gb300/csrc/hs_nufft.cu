@@ -1,11 +1,13 @@
-// De-gridding G_l and gridding G_l^H with the 8 x 8 Kaiser-Bessel window
-// (Sec. 2.1: "G_l has a convolution kernel on its rows"), all channels in one
-// launch, fused with the data-fidelity dual update of Algorithm 2 steps 10-12.
+// De-gridding G_l and gridding G_l^H with the 8 x 8 Kaiser-Bessel window (Sec.
+// 2.1: each row of G_l holds the interpolation kernel of one visibility), all
+// channels in one launch, fused with the data-fidelity dual update of
+// Algorithm 2 steps 10-12.
 //
 // Kernel values are computed on the fly: phi(m + f) for the unit piece m is a
 // fitted polynomial in s = 2 f - 1 (FP32: 9 coefficients, error 7e-9 of phi(0);
-// FP64: 14 coefficients, 6e-15), so the 8 taps of one axis are 8 independent
-// Horner chains at the same s, one per lane.
+// FP64: 14 coefficients, 6e-15). De-gridding evaluates one piece per lane (8
+// independent Horner chains at the same s); gridding evaluates the 8 taps of an
+// axis in one lane as 4 mirrored pairs of even/odd polynomials.
 //
 // De-gridding: 8 lanes per visibility, lane j owns window column j and walks
 // the 8 rows (coalesced 64-byte row segments), then the 8 lanes reduce by
