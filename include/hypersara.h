@@ -514,9 +514,14 @@ HS_API hs_status hs_time_stage(hs_plan_t plan, int stage, const void* in, void* 
  * hs_kb_poly_fit: piecewise polynomial fit of the Kaiser-Bessel kernel used by
  *   the gridding kernels; returns the maximum error relative to phi(0) for
  *   the given number of coefficients per unit interval.
+ * hs_kb_poly_coefs: the fit itself: J x terms doubles, piece p (x in
+ *   [p - J/2, p - J/2 + 1), x = p - J/2 + (s + 1) / 2) as monomial coefficients
+ *   of s in increasing degree. The kernel is even, so piece J - 1 - p at s is
+ *   piece p at -s; the gridding kernels evaluate the two together.
  */
 HS_API hs_status hs_daubechies_lowpass(int p, double* out);
 HS_API hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err);
+HS_API hs_status hs_kb_poly_coefs(int J, double beta, int terms, double* coef_out);
 
 /*
  * hs_sweep_lists (host only): the gridding work lists a plan builds for the

@@ -5,6 +5,8 @@
 #include <memory>
 #include <vector>
 
+#include <algorithm>
+
 #include "hs_internal.h"
 
 namespace hs {
@@ -89,6 +91,16 @@ hs_status hs_kb_poly_fit(int J, double beta, int terms, double* max_rel_err) {
         return fail(HS_ERR_ARG, "hs_kb_poly_fit: need J = 8, 2 <= terms <= 40, beta > 0");
     std::vector<double> c;
     *max_rel_err = kb_poly_fit(J, beta, terms, &c);
+    return HS_OK;
+}
+
+hs_status hs_kb_poly_coefs(int J, double beta, int terms, double* coef_out) {
+    clear_error();
+    if (J != 8 || terms < 2 || terms > 40 || coef_out == nullptr || !(beta > 0))
+        return fail(HS_ERR_ARG, "hs_kb_poly_coefs: need J = 8, 2 <= terms <= 40, beta > 0");
+    std::vector<double> c;
+    kb_poly_fit(J, beta, terms, &c);
+    std::copy(c.begin(), c.end(), coef_out);
     return HS_OK;
 }
 

@@ -104,6 +104,7 @@ _SIGS = {
     "hs_time_stage": ([_P, C.c_int, _P, _P, C.c_int, C.POINTER(C.c_float), _P], C.c_int),
     "hs_daubechies_lowpass": ([C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_kb_poly_fit": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
+    "hs_kb_poly_coefs": ([C.c_int, C.c_double, C.c_int, C.POINTER(C.c_double)], C.c_int),
     "hs_sweep_lists": ([C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, _P, C.POINTER(C.c_int64), _P,
                         C.POINTER(C.c_int64)], C.c_int),
 }
@@ -165,6 +166,13 @@ def kb_poly_fit_error(beta: float, terms: int, J: int = 8) -> float:
     e = C.c_double()
     _check("hs_kb_poly_fit", load().hs_kb_poly_fit(J, beta, terms, C.byref(e)))
     return e.value
+
+
+def kb_poly_coefs(beta: float, terms: int, J: int = 8) -> np.ndarray:
+    """hs_kb_poly_coefs: (J, terms) monomial coefficients in s of every unit piece."""
+    out = (C.c_double * (J * terms))()
+    _check("hs_kb_poly_coefs", load().hs_kb_poly_coefs(J, beta, terms, out))
+    return np.array(out[:], dtype=np.float64).reshape(J, terms)
 
 
 def sweep_lists(Kx: int, Ky: int, offsets, k0x, k0y, hmax: int = 0, cap: int = 0):

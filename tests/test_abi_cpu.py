@@ -87,3 +87,34 @@ def test_static_l2ball_rejects_channel_counts_on_the_host(lib):
         assert "outside" in lib.last_error()
     st = L.hs_proj_l2ball_static(4, None, None, None, None, 0, 0, None, None, None)
     assert st == -1 and "null" in lib.last_error()
+
+
+@pytest.mark.parametrize("terms,tol", [(9, 1e-8), (14, 2e-14)])
+def test_kb_mirrored_pieces_evaluate_the_kernel(lib, terms, tol):
+    """The gridding kernel evaluates the taps of a window as 4 mirrored pairs:
+    piece 7 - m at s and piece m at s are E(s^2) + s O(s^2) and E(s^2) - s O(s^2)
+    of piece 7 - m's even and odd coefficients. That needs the fit's pieces to
+    be mirror images (the kernel is even, Sec. 2.1), and the pair form to give
+    the kernel at both taps to the fit's accuracy (against the oracle's
+    Kaiser-Bessel definition)."""
+    from oracle import kaiser_bessel as kbo
+    beta = kbo.kb_beta(8, 2.0)
+    c = lib.kb_poly_coefs(beta, terms)
+    sign = (-1.0) ** np.arange(terms)
+    for p in range(8):
+        # equal up to the rounding of the conversion to monomials (1e-13 to 1e-11 of the largest)
+        np.testing.assert_allclose(c[7 - p], sign * c[p], rtol=0, atol=1e-10 * np.abs(c).max())
+    peak = kbo.kb(np.array([0.0]), 8, beta)[0]
+    f = np.linspace(0.0, 1.0, 1001, endpoint=False)
+    s = 2.0 * f - 1.0
+    s2 = s * s
+    for m in range(4):
+        ce, co = c[7 - m][0::2], c[7 - m][1::2]
+        E = np.polynomial.polynomial.polyval(s2, ce)
+        O = np.polynomial.polynomial.polyval(s2, co)
+        # window tap m of a window whose start cell is 3 below the cell of the
+        # sample at fraction f: distance m - 3 - f, i.e. piece 7 - m at s; tap 7 - m at 4 - m - f
+        tap_m = kbo.kb(m - 3 - f, 8, beta)
+        tap_mirror = kbo.kb(4 - m - f, 8, beta)
+        assert np.max(np.abs(E + s * O - tap_m)) <= tol * peak
+        assert np.max(np.abs(E - s * O - tap_mirror)) <= tol * peak
